@@ -1,0 +1,214 @@
+/*
+ * swi.h -- C ABI of the GB300 partitioned shift-without-invert eigensolver.
+ *
+ * Method: Feldman & Zhou, "A partitioned shift-without-invert algorithm to
+ * improve parallel eigensolution efficiency in real-space electronic
+ * transport".  The library finds the n_r eigenpairs of smallest real part of
+ * the complex-symmetric operator
+ *
+ *     A = H_KS - i Gamma,   H_KS = -1/2 nabla^2_FD + V(r),          (Eq. 1)
+ *
+ * on a 3D real-space grid, by splitting the real axis into windows j with real
+ * shifts sigma_j, solving each shifted problem (A - sigma_j) U = (eps - sigma_j) U
+ * for the n_r,j eigenvalues closest to sigma_j with a Krylov iteration on the
+ * shifted, never-inverted operator ('SM' selection, Eq. 3), merging the windows
+ * (Algorithm 2), normalising U^T U = I, and evaluating the transmission
+ * T(E) = Tr{G Gamma_R G^dagger Gamma_L} with G(E) = sum_k U_k U_k^T / (E - eps_k)
+ * (Section 1) and its gradients.
+ *
+ * Conventions for every entry point:
+ *  - Grid: nx * ny * nz points, spacing h (bohr); flat index (k*ny + j)*nx + i
+ *    (x fastest).  Hartree units.  The kinetic term is the 12th-order (radius-6)
+ *    central finite difference; each axis needs at least 6 points.
+ *  - Complex numbers are interleaved (re, im) doubles (C99 double _Complex /
+ *    numpy complex128 layout).
+ *  - A block of vectors is row-major [N][ld]: the vector index is innermost
+ *    (element (r, c) at r*ld + c).
+ *  - Pointers flagged `on_device` are CUDA device pointers on the context's
+ *    device; otherwise host pointers.  The library never keeps a caller's
+ *    pointer: inputs are copied before the call returns (device-to-device
+ *    copies are ordered on the context's stream).
+ *  - The library owns every device buffer it allocates.  Pointers returned by
+ *    getters are borrowed and stay valid until the next swi_solve,
+ *    swi_set_eigenpairs or swi_destroy on the same context.
+ *  - Errors are returned as swi_status; no exception crosses the ABI.
+ *    swi_last_error(ctx) gives a message for the last failing call on ctx
+ *    (swi_last_error(NULL) for a failed swi_create).
+ *  - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef SWI_H
+#define SWI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct swi_ctx swi_ctx;
+
+typedef enum {
+  SWI_OK = 0,
+  SWI_EINVAL = 1,    /* invalid argument (size, sign, order, NaN ...) */
+  SWI_ENOMEM = 2,    /* device or host allocation failed */
+  SWI_ECUDA = 3,     /* a CUDA call or kernel failed */
+  SWI_ENOCONV = 4,   /* some window did not converge within its matvec budget */
+  SWI_HOLES = 5,     /* merged windows show an interface without redundancy */
+  SWI_ETIMEOUT = 6,  /* a bounded device wait gave up */
+  SWI_ENOTIMPL = 7,  /* option not implemented */
+  SWI_ESTATE = 8     /* call out of order (e.g. transmission before solve) */
+} swi_status;
+
+enum { SWI_BC_ODD = 0, SWI_BC_ZERO = 1 };        /* boundary rule, see swi_create */
+enum { SWI_PREC_F64 = 0, SWI_PREC_MIXED = 1 };   /* arithmetic of the Krylov loop */
+
+/* Options of swi_solve.  Zero-initialise and set what you need; zero fields
+ * take the defaults given here. */
+typedef struct {
+  int block;            /* b, Krylov block width (default 16; 1..32) */
+  int max_basis;        /* m_j, basis size before a restart (default
+                           max(2 n_req + 1, n_req + 2b) rounded up to b) */
+  int keep;             /* Ritz vectors kept at a restart (default
+                           n_req + (m_j - n_req)/2, at most m_j - b) */
+  int reserved0;
+  long long max_matvecs;/* per-window budget of operator applications per
+                           vector (default 2,000,000) */
+  double rel_tol;       /* convergence: ||A u - eps u|| <= rel_tol ||A||_G ||u||,
+                           ||A||_G the Gershgorin bound (default 1e-10) */
+  double eq_rtol;       /* Algorithm 2 equal-eigenvalue test
+                           |l_m - l_k| <= eq_rtol max(1,|l_k|) (default 1e-8) */
+  double drop_tol;      /* Algorithm 2 redundancy test ||v_k||/||v_k^0|| < drop_tol
+                           (default 1e-6) */
+  unsigned long long seed; /* seed of the random start blocks (default 1) */
+  int n_keep;           /* pairs kept after the merge, lowest real part first
+                           (0 = all merged pairs) */
+  int reserved1;
+} swi_solve_opts;
+
+/* Per-window outcome of swi_solve. */
+typedef struct {
+  double sigma;         /* shift E_S,j */
+  int n_req;            /* requested pairs n_r,j */
+  int n_conv;           /* converged pairs delivered by the window */
+  long long matvecs;    /* operator applications (vectors) */
+  int restarts;
+  int basis;            /* m_j used */
+  double max_res;       /* largest relative residual of the delivered pairs */
+} swi_window_info;
+
+typedef struct {
+  int n_windows;
+  int n_pairs;          /* pairs after merge and selection */
+  int n_converged;      /* of those, pairs whose explicitly recomputed relative
+                           residual is <= rel_tol */
+  int n_duplicates;     /* pairs removed as redundant by Algorithm 2 */
+  int n_holes;          /* interfaces between adjacent windows with no redundancy */
+  int reserved;
+  long long matvecs;    /* total over windows */
+  double max_rel_res;   /* largest explicit relative residual of the kept pairs */
+  double anorm;         /* ||A||_G used for the relative residuals */
+  double t_krylov_s;    /* wall time of the windowed Krylov phase */
+  double t_merge_s;     /* wall time of merge, selection and normalisation */
+} swi_solve_info;
+
+/* Create a context on the current CUDA device.
+ *  bc: SWI_BC_ODD -- psi = 0 on the planes just outside the grid, ghosts by
+ *      odd reflection u[-1-k] = -u[-1+k] (keeps A = A^T exactly);
+ *      SWI_BC_ZERO -- every ghost is zero.
+ *  precision: SWI_PREC_F64 (complex128 vectors, FP64 arithmetic).
+ *  cuda_stream: cudaStream_t (or NULL for the legacy default stream) on which
+ *      every kernel of this context runs.
+ * Errors: SWI_EINVAL (an axis < 6, h <= 0, unknown bc/precision),
+ *         SWI_ENOMEM, SWI_ECUDA. */
+swi_status swi_create(swi_ctx** out, int nx, int ny, int nz, double h, int bc,
+                      int precision, void* cuda_stream);
+
+/* Local potential V(r) of H_KS (Eq. 1), N doubles in Ha.  Errors: SWI_EINVAL
+ * (NULL, non-finite value). */
+swi_status swi_set_potential(swi_ctx* ctx, const double* V, int on_device);
+
+/* Absorbing potentials Gamma_L, Gamma_R (Section 1): N doubles each, >= 0.
+ * A = H_KS - i (Gamma_L + Gamma_R).  Errors: SWI_EINVAL (NULL, negative or
+ * non-finite value). */
+swi_status swi_set_absorber(swi_ctx* ctx, const double* gamma_L, const double* gamma_R,
+                            int on_device);
+
+/* Windows (Eq. 3): p real shifts sigma_j (strictly increasing) and requests
+ * n_req[j] >= 1 (host arrays).  Errors: SWI_EINVAL. */
+swi_status swi_set_windows(swi_ctx* ctx, int p, const double* sigma, const int* n_req);
+
+/* Plan p windows for the lowest n_r pairs with Algorithm 1: counts
+ * n_r,j (round/ceil formulas) and shifts E_S,j = E_S,j-1 + ((E_max-E_min)/N)
+ * (n_r,j + n_r,j-1)/2 with E_S,0 = E_min, n_r,0 = 0.  e_min/e_max are the
+ * extremal real parts.  Requests are inflated: n_req = ceil(n_r,j * inflate).
+ * Writes the plan into sigma_out/n_req_out (host, p entries each, may be NULL)
+ * and sets it as the context's windows.  Errors: SWI_EINVAL. */
+swi_status swi_plan_windows(swi_ctx* ctx, int n_r, int p, double e_min, double e_max,
+                            double inflate, double* sigma_out, int* n_req_out);
+
+/* Apply the shifted operator to a block: Y[:, c] = (A - sigma[c]) X[:, c] for
+ * c < nvec; X and Y are complex128 [N][nvec] (Eq. 3's matrix-vector product,
+ * the hot kernel of the Krylov loop).  sigma is a host array of nvec doubles.
+ * Errors: SWI_EINVAL, SWI_ESTATE (potential/absorber unset), SWI_ECUDA. */
+swi_status swi_apply(swi_ctx* ctx, int nvec, const double* sigma, const void* X, void* Y,
+                     int on_device);
+
+/* Solve all windows (batched on the device), merge them with Algorithm 2,
+ * keep the lowest-real-part pairs and scale them to U^T U = I.
+ * opts may be NULL (defaults); info may be NULL.
+ * Returns SWI_OK, or SWI_ENOCONV / SWI_HOLES with the merged pairs still
+ * available (partial result); SWI_ESTATE if windows/potential are unset. */
+swi_status swi_solve(swi_ctx* ctx, const swi_solve_opts* opts, swi_solve_info* info);
+
+/* Per-window outcome of the last solve: fills up to `cap` entries, returns the
+ * window count in *p. */
+swi_status swi_get_window_info(swi_ctx* ctx, int cap, swi_window_info* out, int* p);
+
+/* Borrowed device pointers to the current pairs: eps complex128[n], U
+ * complex128 [N][ldU] (row-major), U^T U = I.  Errors: SWI_ESTATE (no pairs). */
+swi_status swi_get_eigenpairs(swi_ctx* ctx, int* n, const void** eps_dev, const void** U_dev,
+                              int* ldU);
+
+/* Copy the current pairs out: eps (n complex128), U ([N][n] complex128,
+ * ld = n).  Either pointer may be NULL.  on_device selects the destination. */
+swi_status swi_copy_eigenpairs(swi_ctx* ctx, void* eps, void* U, int on_device);
+
+/* Replace the current pairs with caller-supplied ones (e.g. a previous run's,
+ * Section 2's continuation runs): eps complex128[n], U complex128 [N][n],
+ * assumed to satisfy U^T U = I. */
+swi_status swi_set_eigenpairs(swi_ctx* ctx, int n, const void* eps, const void* U,
+                              int on_device);
+
+/* Explicit relative residuals ||A u_k - eps_k u_k|| / (||A||_G ||u_k||) of the
+ * current pairs (host array of n doubles). */
+swi_status swi_residuals(swi_ctx* ctx, double* res_out);
+
+/* T(E_e) = Tr{G Gamma_R G^dagger Gamma_L} (Section 1) for nE energies through
+ * the spectral G of the current pairs:  R = U^T Gamma_R conj(U),
+ * L = U^T Gamma_L conj(U), W = R o L, T_e = sum_kl g_ek W_kl conj(g_el),
+ * g_ek = 1/(E_e - eps_k).  E, T_out: host arrays of nE doubles.
+ * Errors: SWI_ESTATE (no pairs), SWI_EINVAL. */
+swi_status swi_transmission(swi_ctx* ctx, int nE, const double* E, double* T_out);
+
+/* Vector-Jacobian product of T: given dL/dT_e (nE host doubles), writes
+ * dL/dV(r) = sum_e dLdT_e 2 Re[(G Gamma_R G^dagger Gamma_L G)_rr] with
+ * dG = G dV G in the spectral representation (N doubles, on_device selects
+ * where), and dT_e/dE_e = -2 Re sum_kl g_k^2 W_kl conj(g_l) (nE host doubles).
+ * Either output may be NULL. */
+swi_status swi_grad(swi_ctx* ctx, int nE, const double* E, const double* dLdT, double* dLdV,
+                    int dLdV_on_device, double* dTdE);
+
+/* Message of the last failing call on ctx (thread-local for ctx == NULL). */
+const char* swi_last_error(const swi_ctx* ctx);
+
+/* Number of this library's kernel launches on ctx since creation. */
+long long swi_launch_count(const swi_ctx* ctx);
+
+/* Free every buffer of ctx; NULL is ignored. */
+void swi_destroy(swi_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SWI_H */

@@ -198,6 +198,34 @@ swi_status swi_transmission(swi_ctx* ctx, int nE, const double* E, double* T_out
 swi_status swi_grad(swi_ctx* ctx, int nE, const double* E, const double* dLdT, double* dLdV,
                     int dLdV_on_device, double* dTdE);
 
+/* Per-kernel-class timing (CUDA events on the context's stream), for
+ * roofline accounting.  Classes: */
+enum {
+  SWI_K_STENCIL = 0,  /* shifted stencil (A - sigma) X */
+  SWI_K_GRAM = 1,     /* orthogonalisation inner products C = Q^H W */
+  SWI_K_UPDATE = 2,   /* orthogonalisation update W -= Q C */
+  SWI_K_CHOLQR = 3,   /* Cholesky-QR of each new block */
+  SWI_K_SCHUR = 4,    /* projected eigenproblem (Schur form, SM selection, reordering) */
+  SWI_K_ROTATE = 5,   /* thick-restart rotation Q Z and Ritz vectors */
+  SWI_K_MERGE = 6,    /* Algorithm 2 and normalisation, explicit residuals */
+  SWI_K_PROJ = 7,     /* Gamma-weighted projections U^H Gamma U of T(E) */
+  SWI_K_TRANS = 8,    /* T(E) and dT/dE contraction */
+  SWI_K_GRAD = 9,     /* adjoint dL/dV */
+  SWI_K_COUNT = 10
+};
+typedef struct {
+  long long launches; /* timed launch groups */
+  double ms;          /* summed device time */
+  double flops;       /* algorithmic floating-point operations (FMA = 2) */
+  double bytes;       /* algorithmic HBM bytes (each operand read once, output written once) */
+} swi_kernel_stats;
+
+/* enable != 0: start recording (and clear previous records); 0: stop. */
+swi_status swi_profile(swi_ctx* ctx, int enable);
+
+/* Synchronise the stream and sum the records per class into out[SWI_K_COUNT]. */
+swi_status swi_profile_read(swi_ctx* ctx, swi_kernel_stats* out);
+
 /* Message of the last failing call on ctx (thread-local for ctx == NULL). */
 const char* swi_last_error(const swi_ctx* ctx);
 

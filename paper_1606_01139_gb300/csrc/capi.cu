@@ -1,0 +1,1078 @@
+// C ABI and host-side runtime of the partitioned shift-without-invert solver.
+//
+// The host plans and sequences; every O(N) step runs in this library's
+// kernels on the context's stream.  One solve batches all windows (the
+// paper's independent partitions, Section 2.1) into shared launches: the
+// stencil applies (A - sigma_j) to the new block of every active window in one
+// launch, the orthogonalisation and Cholesky-QR of all windows go out as
+// batched launches, and windows that reach their maximum basis restart
+// together.  The host reads back only a few status words per restart.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "merge.cuh"
+#include "swi_internal.cuh"
+#include "transport.cuh"
+
+using swi::Error;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+// 12th-order central second-difference weights (radius 6), c_0..c_6.
+// Algorithmic FP64 flops of the stencil per grid point and vector: 18 neighbour
+// pairs x (2 adds + 2 FMA) + the local term (2 MUL + 2 FMA) + the shift (2 adds).
+constexpr double kStencilFlops = 18.0 * 6.0 + 6.0 + 2.0;
+
+const double kFD[7] = {-5369.0 / 1800.0, 12.0 / 7.0, -15.0 / 56.0, 10.0 / 189.0,
+                       -1.0 / 112.0,     2.0 / 1925.0, -1.0 / 16632.0};
+
+struct DevMem {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevMem() = default;
+  DevMem(const DevMem&) = delete;
+  DevMem& operator=(const DevMem&) = delete;
+  ~DevMem() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  void ensure(size_t nbytes) {
+    if (nbytes <= bytes) return;
+    release();
+    if (nbytes == 0) return;
+    cudaError_t e = cudaMalloc(&p, nbytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+      throw Error{SWI_ENOMEM, "cudaMalloc of " + std::to_string(nbytes) + " bytes failed"};
+    }
+    bytes = nbytes;
+  }
+  template <class T>
+  T* as() const {
+    return static_cast<T*>(p);
+  }
+};
+
+struct Window {
+  double sigma = 0.0;
+  int nreq = 0, m = 0, keep = 0, ld = 0;  // ld: columns of the Q buffers (m + b)
+  DevMem Q[2], W, H, Bm, Z, S, Bz, theta, resid, C1, C2, G, R1, R1i, R2, R2i, Zext, Yw, eps_w, res_w;
+  int cur = 0, p = 0;
+  bool done = false, failed = false;
+  long long matvecs = 0;
+  int restarts = 0;
+  int nconv = 0;
+  double max_res = 0.0;
+};
+
+}  // namespace
+
+struct swi_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int nx = 0, ny = 0, nz = 0, N = 0;
+  double h = 0.0;
+  int bc = SWI_BC_ODD, precision = SWI_PREC_F64;
+  DevMem V, G, gL, gR;
+  bool has_V = false, has_G = false;
+  double maxabsV = 0.0, maxG = 0.0;
+  std::vector<double> sigma;
+  std::vector<int> nreq;
+  // current pairs
+  int npairs = 0;
+  DevMem eps, U;  // [n], [N][n]
+  std::vector<double> resid;
+  std::vector<swi_window_info> winfo;
+  // transport cache
+  bool have_RL = false;
+  DevMem MR, ML, Rm, Lm, Wm, Mg, Ebuf, Tbuf, dEbuf, wbuf;
+  // workspaces
+  DevMem gram_work, sig_dev, colwork, scratch, Uall, ordinfo, cholstat, ptrs, dres;
+  // merge scratch
+  DevMem m_comp, m_pairs, m_counts, m_work, m_gram, m_kept, m_order, m_holes, m_src, m_coef, m_nterm, m_info,
+      m_win, m_eps_all, m_eps_out;
+  long long launches = 0;
+  std::string err;
+  // per-kernel-class event timing
+  struct ProfRec {
+    int kind;
+    cudaEvent_t a, b;
+    double flops, bytes;
+  };
+  bool prof_on = false;
+  std::vector<ProfRec> prof;
+  std::vector<cudaEvent_t> evpool;
+  ~swi_ctx() {
+    for (auto& r : prof) {
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+    for (auto e : evpool) cudaEventDestroy(e);
+  }
+};
+
+namespace {
+
+cudaEvent_t take_event(swi_ctx* c) {
+  if (!c->evpool.empty()) {
+    cudaEvent_t e = c->evpool.back();
+    c->evpool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  SWI_CUDA_TRY(cudaEventCreate(&e));
+  return e;
+}
+
+// Records CUDA events around the launches of its scope when profiling is on.
+struct ProfScope {
+  swi_ctx* c;
+  int kind;
+  double flops, bytes;
+  cudaEvent_t a = nullptr;
+  ProfScope(swi_ctx* ctx, int k, double f, double by) : c(ctx), kind(k), flops(f), bytes(by) {
+    if (c->prof_on) {
+      a = take_event(c);
+      SWI_CUDA_TRY(cudaEventRecord(a, c->stream));
+    }
+  }
+  ~ProfScope() {
+    if (!a) return;
+    cudaEvent_t b = nullptr;
+    if (!c->evpool.empty()) {
+      b = c->evpool.back();
+      c->evpool.pop_back();
+    } else if (cudaEventCreate(&b) != cudaSuccess) {
+      return;
+    }
+    if (cudaEventRecord(b, c->stream) != cudaSuccess) return;
+    c->prof.push_back({kind, a, b, flops, bytes});
+  }
+};
+
+swi_status fail(swi_ctx* ctx, swi_status code, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  else g_create_error = msg;
+  return code;
+}
+
+template <class F>
+swi_status guarded(swi_ctx* ctx, F&& f) {
+  if (!ctx) return fail(nullptr, SWI_EINVAL, "null context");
+  try {
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return fail(ctx, SWI_ECUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+    return f();
+  } catch (const Error& e) {
+    return fail(ctx, e.code, e.msg);
+  } catch (const std::bad_alloc&) {
+    return fail(ctx, SWI_ENOMEM, "host allocation failed");
+  } catch (...) {
+    return fail(ctx, SWI_ECUDA, "unexpected exception");
+  }
+}
+
+swi::StencilParams stencil_params(const swi_ctx* c) {
+  swi::StencilParams P;
+  P.nx = c->nx;
+  P.ny = c->ny;
+  P.nz = c->nz;
+  P.bc = c->bc;
+  for (int m = 0; m < 7; ++m) P.cm[m] = -kFD[m] / (2.0 * c->h * c->h);
+  P.V = c->V.as<double>();
+  P.G = c->G.as<double>();
+  return P;
+}
+
+double gershgorin(const swi_ctx* c) {
+  double s = std::fabs(kFD[0]);
+  for (int m = 1; m < 7; ++m) s += 2.0 * std::fabs(kFD[m]);
+  return 3.0 * 0.5 / (c->h * c->h) * s + c->maxabsV + c->maxG;
+}
+
+void copy_in(DevMem& dst, const void* src, size_t bytes, bool on_device, cudaStream_t s) {
+  dst.ensure(bytes);
+  SWI_CUDA_TRY(cudaMemcpyAsync(dst.p, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+}
+
+void sync(cudaStream_t s) { SWI_CUDA_TRY(cudaStreamSynchronize(s)); }
+
+// Y[:, c] = (A - sigma_c) X[:, c] in chunks of columns, sigma from the context's sigma table
+void apply_block(swi_ctx* c, const double2* X, int ldx, double2* Y, int ldy, int ncols) {
+  const swi::StencilParams P = stencil_params(c);
+  for (int c0 = 0; c0 < ncols; c0 += 32) {
+    swi::StencilBatch bt;
+    bt.n = 1;
+    bt.blk[0] = swi::StencilBlock{X + c0, Y + c0, ldx, ldy, std::min(32, ncols - c0), c0};
+    swi::launch_stencil(P, bt, c->sig_dev.as<double>(), c->stream, &c->launches);
+  }
+}
+
+// explicit relative residuals of (eps, U) -> host vector
+void explicit_residuals(swi_ctx* c, const double2* Ud, int ldu, const double2* epsd, int n, std::vector<double>& out) {
+  out.assign(n, 0.0);
+  if (n == 0) return;
+  c->sig_dev.ensure(sizeof(double) * std::max(n, 64));
+  SWI_CUDA_TRY(cudaMemsetAsync(c->sig_dev.p, 0, sizeof(double) * n, c->stream));
+  c->scratch.ensure(sizeof(double2) * (size_t)c->N * n);
+  apply_block(c, Ud, ldu, c->scratch.as<double2>(), n, n);
+  c->colwork.ensure(sizeof(double) * (size_t)n * 1024);
+  c->dres.ensure(sizeof(double) * 2 * n);
+  // ||u_k|| and ||A u_k - eps_k u_k||
+  swi::launch_colnorm_resid(Ud, ldu, Ud, ldu, nullptr, n, c->N, c->dres.as<double>() + n, c->colwork.as<double>(),
+                            c->colwork.bytes / sizeof(double), c->stream, &c->launches);
+  swi::launch_colnorm_resid(Ud, ldu, c->scratch.as<double2>(), n, epsd, n, c->N, c->dres.as<double>(),
+                            c->colwork.as<double>(), c->colwork.bytes / sizeof(double), c->stream, &c->launches);
+  std::vector<double> both(2 * n);
+  SWI_CUDA_TRY(cudaMemcpyAsync(both.data(), c->dres.p, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, c->stream));
+  sync(c->stream);
+  std::vector<double> unorm(both.begin() + n, both.end());
+  std::copy(both.begin(), both.begin() + n, out.begin());
+  const double an = gershgorin(c);
+  for (int k = 0; k < n; ++k) out[k] = out[k] / (an * std::max(unorm[k], 1e-300));
+}
+
+void gram_work_ensure(swi_ctx* c, size_t elems) {
+  c->gram_work.ensure(sizeof(double2) * std::max<size_t>(elems, 1 << 20));
+}
+
+// Cholesky-QR2 of the blocks W_j (N x b, ld b) into Q_j[:, col : col+b]; R1, R2 kept per window.
+void cholqr2(swi_ctx* c, std::vector<Window*>& ws, const std::vector<int>& col, int b) {
+  const int nb = (int)ws.size();
+  if (nb == 0) return;
+  // device pointer tables for the Cholesky kernel: [G..., R..., Rinv...]
+  c->ptrs.ensure(sizeof(void*) * 3 * swi::kMaxBatch);
+  c->cholstat.ensure(sizeof(int) * swi::kMaxBatch);
+  auto gram_of = [&](bool second) {
+    swi::GramBatch gb;
+    gb.n = nb;
+    for (int q = 0; q < nb; ++q) {
+      Window& w = *ws[q];
+      const double2* X = second ? w.Q[w.cur].as<double2>() + col[q] : w.W.as<double2>();
+      const int ldx = second ? w.ld : b;
+      gb.job[q] = swi::GramJob{X, X, w.G.as<double2>(), ldx, ldx, b, b, b, 0};
+    }
+    swi::launch_gram(gb, c->N, nullptr, 0, c->gram_work.as<double2>(), c->gram_work.bytes / sizeof(double2),
+                     c->stream, &c->launches);
+  };
+  auto chol_of = [&](bool second) {
+    swi::CholBatch cb;
+    cb.n = nb;
+    for (int q = 0; q < nb; ++q) {
+      cb.G[q] = ws[q]->G.as<double2>();
+      cb.R[q] = (second ? ws[q]->R2 : ws[q]->R1).as<double2>();
+      cb.Rinv[q] = (second ? ws[q]->R2i : ws[q]->R1i).as<double2>();
+    }
+    swi::launch_chol_batch(cb, b, c->cholstat.as<int>(), c->stream, &c->launches);
+  };
+  gram_of(false);
+  chol_of(false);
+  {
+    swi::RowGemmBatch rb;
+    rb.n = nb;
+    for (int q = 0; q < nb; ++q) {
+      Window& w = *ws[q];
+      rb.job[q] = swi::RowGemmJob{w.W.as<double2>(), w.R1i.as<double2>(), nullptr, w.Q[w.cur].as<double2>() + col[q],
+                                  b, b, 0, w.ld, b, b, 1.0, 0.0};
+    }
+    swi::launch_rowgemm(rb, c->N, c->stream, &c->launches);
+  }
+  gram_of(true);
+  chol_of(true);
+  {
+    swi::RowGemmBatch rb;
+    rb.n = nb;
+    for (int q = 0; q < nb; ++q) {
+      Window& w = *ws[q];
+      rb.job[q] = swi::RowGemmJob{w.Q[w.cur].as<double2>() + col[q], w.R2i.as<double2>(), nullptr, w.W.as<double2>(),
+                                  w.ld, b, 0, b, b, b, 1.0, 0.0};
+    }
+    swi::launch_rowgemm(rb, c->N, c->stream, &c->launches);
+  }
+  for (int q = 0; q < nb; ++q) {
+    Window& w = *ws[q];
+    swi::launch_copy_block(w.W.as<double2>(), b, w.Q[w.cur].as<double2>() + col[q], w.ld, c->N, b, c->stream,
+                           &c->launches);
+  }
+}
+
+swi_status do_solve(swi_ctx* c, const swi_solve_opts* o, swi_solve_info* info) {
+  if (!c->has_V || !c->has_G) return fail(c, SWI_ESTATE, "potential and absorbers must be set before solve");
+  if (c->sigma.empty()) return fail(c, SWI_ESTATE, "windows must be set before solve");
+  swi_solve_opts opt;
+  std::memset(&opt, 0, sizeof(opt));
+  if (o) opt = *o;
+  const int b = opt.block > 0 ? opt.block : 16;
+  if (b > 32) return fail(c, SWI_EINVAL, "block width must be <= 32");
+  const double rel_tol = opt.rel_tol > 0 ? opt.rel_tol : 1e-10;
+  const double eq_rtol = opt.eq_rtol > 0 ? opt.eq_rtol : 1e-8;
+  const double drop_tol = opt.drop_tol > 0 ? opt.drop_tol : 1e-6;
+  const long long budget = opt.max_matvecs > 0 ? opt.max_matvecs : 2000000LL;
+  const unsigned long long seed = opt.seed ? opt.seed : 1ull;
+  const double anorm = gershgorin(c);
+  const int nwin = (int)c->sigma.size();
+  if (nwin > swi::kMaxBatch) return fail(c, SWI_EINVAL, "at most 64 windows per solve");
+  const double t0 = swi::now_seconds();
+
+  // ---- per-window sizes and buffers
+  std::vector<std::unique_ptr<Window>> win(nwin);
+  size_t total_out = 0;
+  for (int j = 0; j < nwin; ++j) {
+    win[j].reset(new Window());
+    Window& w = *win[j];
+    w.sigma = c->sigma[j];
+    w.nreq = c->nreq[j];
+    int keep = opt.keep > 0 ? opt.keep : std::max(w.nreq + (w.nreq + 1) / 2, w.nreq + b);
+    int m = opt.max_basis > 0 ? opt.max_basis : std::max(2 * w.nreq + 1, keep + 8 * b);
+    m = (m + b - 1) / b * b;
+    if (keep > m - b) keep = m - b;
+    if (keep < w.nreq) return fail(c, SWI_EINVAL, "max_basis too small for the window request");
+    if (m > 1024) return fail(c, SWI_EINVAL, "basis larger than 1024 is not supported");
+    if (m + b > c->N) return fail(c, SWI_EINVAL, "basis larger than the problem dimension");
+    w.m = m;
+    w.keep = keep;
+    w.ld = m + b;
+    const size_t N = c->N;
+    w.Q[0].ensure(sizeof(double2) * N * w.ld);
+    w.Q[1].ensure(sizeof(double2) * N * w.ld);
+    w.W.ensure(sizeof(double2) * N * b);
+    w.H.ensure(sizeof(double2) * w.ld * w.ld);
+    w.Z.ensure(sizeof(double2) * w.ld * w.ld);
+    w.S.ensure(sizeof(double2) * w.ld * w.ld);
+    w.Bm.ensure(sizeof(double2) * b * w.ld);
+    w.Bz.ensure(sizeof(double2) * b * w.ld);
+    w.theta.ensure(sizeof(double2) * w.ld);
+    w.resid.ensure(sizeof(double) * w.ld);
+    w.C1.ensure(sizeof(double2) * w.ld * b);
+    w.C2.ensure(sizeof(double2) * w.ld * b);
+    w.G.ensure(sizeof(double2) * b * b);
+    w.R1.ensure(sizeof(double2) * b * b);
+    w.R1i.ensure(sizeof(double2) * b * b);
+    w.R2.ensure(sizeof(double2) * b * b);
+    w.R2i.ensure(sizeof(double2) * b * b);
+    w.Zext.ensure(sizeof(double2) * w.ld * w.ld);
+    w.Yw.ensure(sizeof(double2) * w.ld * w.nreq);
+    w.eps_w.ensure(sizeof(double2) * w.nreq);
+    w.res_w.ensure(sizeof(double) * w.nreq);
+    total_out += w.nreq;
+  }
+  const int n_all = (int)total_out;
+  c->Uall.ensure(sizeof(double2) * (size_t)c->N * n_all);
+  c->ordinfo.ensure(sizeof(int) * 4 * nwin);
+  gram_work_ensure(c, (size_t)4 << 20);
+  // per-column shift table for the batched stencil
+  {
+    std::vector<double> sg((size_t)nwin * b);
+    for (int j = 0; j < nwin; ++j)
+      for (int q = 0; q < b; ++q) sg[(size_t)j * b + q] = c->sigma[j];
+    c->sig_dev.ensure(sizeof(double) * std::max<size_t>(sg.size(), 64));
+    SWI_CUDA_TRY(cudaMemcpyAsync(c->sig_dev.p, sg.data(), sizeof(double) * sg.size(), cudaMemcpyHostToDevice,
+                                 c->stream));
+    sync(c->stream);
+  }
+
+  // ---- start blocks: random, orthonormalised
+  {
+    std::vector<Window*> ws;
+    std::vector<int> col;
+    for (int j = 0; j < nwin; ++j) {
+      Window& w = *win[j];
+      swi::launch_random_block(w.W.as<double2>(), b, 0, b, c->N, seed * 1000003ull + j, c->stream, &c->launches);
+      ws.push_back(&w);
+      col.push_back(0);
+    }
+    cholqr2(c, ws, col, b);
+  }
+
+  const swi::StencilParams P = stencil_params(c);
+  const double tol_abs = rel_tol * anorm;
+  std::vector<int> out_off(nwin);
+  {
+    int o2 = 0;
+    for (int j = 0; j < nwin; ++j) {
+      out_off[j] = o2;
+      o2 += win[j]->nreq;
+    }
+  }
+
+  // ---- the batched Krylov-Schur loop
+  const long long max_steps = 100000000LL;
+  for (long long step = 0; step < max_steps; ++step) {
+    std::vector<Window*> act;
+    std::vector<int> idx;
+    for (int j = 0; j < nwin; ++j)
+      if (!win[j]->done) {
+        act.push_back(win[j].get());
+        idx.push_back(j);
+      }
+    if (act.empty()) break;
+    const int na = (int)act.size();
+    // 1) W_j = (A - sigma_j) V_j for every active window, one launch
+    {
+      swi::StencilBatch sb;
+      sb.n = na;
+      for (int q = 0; q < na; ++q) {
+        Window& w = *act[q];
+        if (w.p + 2 * b > w.ld) throw Error{SWI_ECUDA, "internal: Krylov block beyond the basis buffer"};
+        sb.blk[q] = swi::StencilBlock{w.Q[w.cur].as<double2>() + w.p, w.W.as<double2>(), w.ld, b, b, idx[q] * b};
+      }
+      const double Nn = (double)c->N;
+      ProfScope ps(c, SWI_K_STENCIL, kStencilFlops * Nn * b * na, (32.0 * b + 16.0) * Nn * na);
+      swi::launch_stencil(P, sb, c->sig_dev.as<double>(), c->stream, &c->launches);
+    }
+    // 2) block classical Gram-Schmidt, twice, against [Q_j V_j]
+    for (int pass = 0; pass < 2; ++pass) {
+      swi::GramBatch gb;
+      gb.n = na;
+      swi::RowGemmBatch rb;
+      rb.n = na;
+      double ncol = 0.0;
+      for (int q = 0; q < na; ++q) {
+        Window& w = *act[q];
+        double2* C = (pass == 0 ? w.C1 : w.C2).as<double2>();
+        gb.job[q] = swi::GramJob{w.Q[w.cur].as<double2>(), w.W.as<double2>(), C, w.ld, b, b, w.p + b, b, 0};
+        rb.job[q] = swi::RowGemmJob{w.Q[w.cur].as<double2>(), C, w.W.as<double2>(), w.W.as<double2>(),
+                                    w.ld, b, b, b, w.p + b, b, -1.0, 1.0};
+        ncol += w.p + b;
+      }
+      const double Nn = (double)c->N;
+      {
+        ProfScope ps(c, SWI_K_GRAM, 8.0 * Nn * ncol * b, 16.0 * Nn * (ncol + na * b));
+        swi::launch_gram(gb, c->N, nullptr, 0, c->gram_work.as<double2>(), c->gram_work.bytes / sizeof(double2),
+                         c->stream, &c->launches);
+      }
+      {
+        ProfScope ps(c, SWI_K_UPDATE, 8.0 * Nn * ncol * b, 16.0 * Nn * (ncol + 2.0 * na * b));
+        swi::launch_rowgemm(rb, c->N, c->stream, &c->launches);
+      }
+    }
+    // 3) Cholesky-QR2 of the remainder into Q_j[:, p+b : p+2b]
+    {
+      std::vector<int> col(na);
+      for (int q = 0; q < na; ++q) col[q] = act[q]->p + b;
+      const double Nn = (double)c->N;
+      ProfScope ps(c, SWI_K_CHOLQR, 4.0 * 8.0 * Nn * b * b * na, 5.0 * 16.0 * Nn * b * na);
+      cholqr2(c, act, col, b);
+    }
+    // 4) projected matrix and coupling rows
+    {
+      swi::HUpdBatch hb;
+      hb.n = na;
+      for (int q = 0; q < na; ++q) {
+        Window& w = *act[q];
+        hb.job[q] = swi::HUpdJob{w.H.as<double2>(), w.Bm.as<double2>(), w.C1.as<double2>(), w.C2.as<double2>(),
+                                 w.R1.as<double2>(), w.R2.as<double2>(), w.ld, w.p, b};
+      }
+      swi::launch_hupdate_batch(hb, c->stream, &c->launches);
+    }
+    std::vector<Window*> rs;
+    std::vector<int> rsi;
+    for (int q = 0; q < na; ++q) {
+      Window& w = *act[q];
+      w.p += b;
+      w.matvecs += b;
+      if (w.p + b > w.m) {  // the next block would not fit: restart on the current basis
+        rs.push_back(&w);
+        rsi.push_back(idx[q]);
+      }
+    }
+    if (rs.empty()) continue;
+    // 5) restart: Schur form, SM selection, reordering, residual estimates
+    const int nr = (int)rs.size();
+    {
+      swi::SchurBatch sb;
+      sb.n = nr;
+      for (int q = 0; q < nr; ++q) {
+        Window& w = *rs[q];
+        if (w.p > w.m || w.keep + b > w.m)
+          throw Error{SWI_ECUDA, "internal: basis bookkeeping out of range"};
+        // As ARPACK does, keep more Ritz vectors once some wanted pairs have
+        // converged, so the rest keep room in the restarted basis.
+        const int keep_eff = std::min(w.m - b, w.keep + std::min(w.nconv, (w.m - w.keep) / 2));
+        sb.job[q] = swi::SchurJob{w.H.as<double2>(), w.Z.as<double2>(), w.Bm.as<double2>(), w.Bz.as<double2>(),
+                                  w.theta.as<double2>(), w.resid.as<double>(), w.S.as<double2>(),
+                                  c->ordinfo.as<int>() + 4 * q, w.p, w.ld, b, keep_eff, w.nreq, w.m - b, tol_abs};
+      }
+      ProfScope ps(c, SWI_K_SCHUR, 0.0, 0.0);
+      swi::launch_schur_batch(sb, c->stream, &c->launches);
+    }
+    std::vector<int> oi(4 * nr);
+    SWI_CUDA_TRY(cudaMemcpyAsync(oi.data(), c->ordinfo.p, sizeof(int) * 4 * nr, cudaMemcpyDeviceToHost, c->stream));
+    sync(c->stream);
+    swi::RitzBatch fin;
+    fin.n = 0;
+    std::vector<Window*> fin_w;
+    std::vector<int> fin_i;
+    swi::ZextBatch zb;
+    zb.n = 0;
+    std::vector<Window*> rot_w;
+    std::vector<int> rot_k;
+    for (int q = 0; q < nr; ++q) {
+      Window& w = *rs[q];
+      const int k = oi[4 * q], nconv = oi[4 * q + 1], st = oi[4 * q + 2];
+      w.restarts++;
+      w.nconv = nconv;
+      if (st != 0) w.failed = true;
+      if (st != 0 || nconv >= w.nreq || w.matvecs >= budget) {
+        fin.job[fin.n++] = swi::RitzJob{w.Z.as<double2>(), w.S.as<double2>(), w.theta.as<double2>(),
+                                        w.resid.as<double>(), c->ordinfo.as<int>() + 4 * q, w.Yw.as<double2>(),
+                                        w.eps_w.as<double2>(), w.res_w.as<double>(), w.p, w.ld, w.nreq, w.nreq,
+                                        w.sigma};
+        fin_w.push_back(&w);
+        fin_i.push_back(rsi[q]);
+      } else {
+        if (k + b > w.m || k < w.nreq) throw Error{SWI_ECUDA, "internal: restart size out of range"};
+        zb.job[zb.n++] = swi::ZextJob{w.Z.as<double2>(), w.Zext.as<double2>(), w.ld, k + b, w.p, k, b};
+        rot_w.push_back(&w);
+        rot_k.push_back(k);
+      }
+    }
+    if (fin.n) {
+      swi::RowGemmBatch rb;
+      rb.n = fin.n;
+      double fl = 0.0, by = 0.0;
+      for (int q = 0; q < fin.n; ++q) {
+        Window& w = *fin_w[q];
+        rb.job[q] = swi::RowGemmJob{w.Q[w.cur].as<double2>(), w.Yw.as<double2>(), nullptr,
+                                    c->Uall.as<double2>() + out_off[fin_i[q]], w.ld, w.nreq, 0, n_all, w.p, w.nreq,
+                                    1.0, 0.0};
+        w.done = true;
+        fl += 8.0 * c->N * (double)w.p * w.nreq;
+        by += 16.0 * c->N * (double)(w.p + w.nreq);
+      }
+      ProfScope ps(c, SWI_K_ROTATE, fl, by);
+      swi::launch_ritz_batch(fin, c->stream, &c->launches);
+      swi::launch_rowgemm(rb, c->N, c->stream, &c->launches);
+    }
+    if (zb.n) {
+      swi::RowGemmBatch rb;
+      rb.n = zb.n;
+      double fl = 0.0, by = 0.0;
+      for (int q = 0; q < zb.n; ++q) {
+        Window& w = *rot_w[q];
+        const int k = rot_k[q];
+        rb.job[q] = swi::RowGemmJob{w.Q[w.cur].as<double2>(), w.Zext.as<double2>(), nullptr,
+                                    w.Q[1 - w.cur].as<double2>(), w.ld, k + b, 0, w.ld, w.p + b, k + b, 1.0, 0.0};
+        fl += 8.0 * c->N * (double)(w.p + b) * (k + b);
+        by += 16.0 * c->N * (double)(w.p + b + k + b);
+      }
+      ProfScope ps(c, SWI_K_ROTATE, fl, by);
+      swi::launch_zext_batch(zb, c->stream, &c->launches);
+      swi::launch_rowgemm(rb, c->N, c->stream, &c->launches);
+      for (int q = 0; q < zb.n; ++q) {
+        Window& w = *rot_w[q];
+        const int k = rot_k[q];
+        w.cur = 1 - w.cur;
+        swi::launch_copy_block(w.Bz.as<double2>(), w.ld, w.Bm.as<double2>(), w.ld, b, k, c->stream, &c->launches);
+        w.p = k;
+      }
+    }
+  }
+  // ---- gather eigenvalue estimates and window statistics
+  std::vector<double2> eps_all(n_all);
+  std::vector<int> win_of(n_all);
+  c->winfo.assign(nwin, swi_window_info());
+  bool any_fail = false, any_noconv = false;
+  for (int j = 0; j < nwin; ++j) {
+    Window& w = *win[j];
+    std::vector<double> rw(w.nreq);
+    SWI_CUDA_TRY(cudaMemcpyAsync(eps_all.data() + out_off[j], w.eps_w.p, sizeof(double2) * w.nreq,
+                                 cudaMemcpyDeviceToHost, c->stream));
+    SWI_CUDA_TRY(cudaMemcpyAsync(rw.data(), w.res_w.p, sizeof(double) * w.nreq, cudaMemcpyDeviceToHost, c->stream));
+    sync(c->stream);
+    for (int q = 0; q < w.nreq; ++q) win_of[out_off[j] + q] = j;
+    swi_window_info& wi = c->winfo[j];
+    wi.sigma = w.sigma;
+    wi.n_req = w.nreq;
+    wi.n_conv = w.nconv;
+    wi.matvecs = w.matvecs;
+    wi.restarts = w.restarts;
+    wi.basis = w.m;
+    double mr = 0.0;
+    for (double r : rw) mr = std::max(mr, r / anorm);
+    wi.max_res = mr;
+    any_fail |= w.failed;
+    any_noconv |= (w.nconv < w.nreq);
+  }
+  win.clear();  // free the Krylov bases before the merge
+  const double t1 = swi::now_seconds();
+
+  // ---- Algorithm 2 merge, selection, U^T U = I
+  const int pair_cap = std::max(4 * n_all, 1024);
+  c->m_eps_all.ensure(sizeof(double2) * n_all);
+  c->m_win.ensure(sizeof(int) * n_all);
+  SWI_CUDA_TRY(cudaMemcpyAsync(c->m_eps_all.p, eps_all.data(), sizeof(double2) * n_all, cudaMemcpyHostToDevice,
+                               c->stream));
+  SWI_CUDA_TRY(cudaMemcpyAsync(c->m_win.p, win_of.data(), sizeof(int) * n_all, cudaMemcpyHostToDevice, c->stream));
+  c->m_comp.ensure(sizeof(int) * n_all);
+  c->m_pairs.ensure(sizeof(int) * 2 * pair_cap);
+  c->m_counts.ensure(sizeof(int) * 4);
+  c->m_work.ensure(sizeof(double2) * (size_t)pair_cap * 2 * 304);
+  c->m_gram.ensure(sizeof(double2) * 2 * pair_cap);
+  c->m_kept.ensure(sizeof(int) * n_all);
+  c->m_order.ensure(sizeof(int) * n_all);
+  c->m_holes.ensure(sizeof(int) * (nwin + 1));
+  c->m_src.ensure(sizeof(int) * swi::merge_src_elems(n_all));
+  c->m_coef.ensure(sizeof(double2) * swi::merge_coef_elems(n_all));
+  c->m_nterm.ensure(sizeof(int) * (n_all + 1));
+  c->m_info.ensure(sizeof(int) * 4);
+  c->m_eps_out.ensure(sizeof(double2) * n_all);
+  swi::MergeArgs ma;
+  ma.U = c->Uall.as<double2>();
+  ma.ldu = n_all;
+  ma.N = c->N;
+  ma.n = n_all;
+  ma.p = nwin;
+  ma.eps = c->m_eps_all.as<double2>();
+  ma.win = c->m_win.as<int>();
+  ma.eq_rtol = eq_rtol;
+  ma.drop_tol = drop_tol;
+  ma.n_keep = opt.n_keep;
+  ma.comp = c->m_comp.as<int>();
+  ma.pairs = c->m_pairs.as<int>();
+  ma.pair_cap = pair_cap;
+  ma.counts = c->m_counts.as<int>();
+  ma.work = c->m_work.as<double2>();
+  ma.work_elems = c->m_work.bytes / sizeof(double2);
+  ma.gram = c->m_gram.as<double2>();
+  ma.kept = c->m_kept.as<int>();
+  ma.order = c->m_order.as<int>();
+  ma.holes = c->m_holes.as<int>();
+  ma.src = c->m_src.as<int>();
+  ma.coef = c->m_coef.as<double2>();
+  ma.nterm = c->m_nterm.as<int>();
+  ma.out_eps = c->m_eps_out.as<double2>();
+  ma.info = c->m_info.as<int>();
+  {
+    ProfScope ps(c, SWI_K_MERGE, 0.0, 16.0 * c->N * (double)n_all);
+    swi::merge_run(ma, c->stream, &c->launches);
+  }
+  int minfo[4];
+  SWI_CUDA_TRY(cudaMemcpyAsync(minfo, c->m_info.p, sizeof(int) * 4, cudaMemcpyDeviceToHost, c->stream));
+  sync(c->stream);
+  const int nout = minfo[0];
+  c->U.ensure(sizeof(double2) * (size_t)c->N * std::max(nout, 1));
+  c->eps.ensure(sizeof(double2) * std::max(nout, 1));
+  ma.out_U = c->U.as<double2>();
+  ma.ldo = nout;
+  {
+    ProfScope ps(c, SWI_K_MERGE, 0.0, 16.0 * c->N * (double)(n_all + nout));
+    swi::merge_apply(ma, nout, c->stream, &c->launches);
+  }
+  SWI_CUDA_TRY(cudaMemcpyAsync(c->eps.p, c->m_eps_out.p, sizeof(double2) * nout, cudaMemcpyDeviceToDevice, c->stream));
+  c->npairs = nout;
+  c->have_RL = false;
+  c->Uall.release();
+  // explicit FP64 residuals of the delivered pairs
+  {
+    ProfScope ps(c, SWI_K_MERGE, kStencilFlops * c->N * (double)nout, 48.0 * c->N * (double)nout);
+    explicit_residuals(c, c->U.as<double2>(), nout, c->eps.as<double2>(), nout, c->resid);
+  }
+  const double t2 = swi::now_seconds();
+  int nconv = 0;
+  double maxr = 0.0;
+  for (double r : c->resid) {
+    if (r <= rel_tol) ++nconv;
+    maxr = std::max(maxr, r);
+  }
+  long long mv = 0;
+  for (auto& wi : c->winfo) mv += wi.matvecs;
+  if (info) {
+    info->n_windows = nwin;
+    info->n_pairs = nout;
+    info->n_converged = nconv;
+    info->n_duplicates = minfo[1];
+    info->n_holes = minfo[2];
+    info->matvecs = mv;
+    info->max_rel_res = maxr;
+    info->anorm = anorm;
+    info->t_krylov_s = t1 - t0;
+    info->t_merge_s = t2 - t1;
+  }
+  if (any_fail) return fail(c, SWI_ENOCONV, "a window's projected eigenproblem did not converge");
+  if (minfo[3] != 0) return fail(c, SWI_EINVAL, "merge: equal-eigenvalue component too large");
+  if (any_noconv) return fail(c, SWI_ENOCONV, "some window did not converge within its matvec budget");
+  if (minfo[2] > 0) return fail(c, SWI_HOLES, std::to_string(minfo[2]) + " interface(s) without redundancy");
+  return SWI_OK;
+}
+
+void ensure_RL(swi_ctx* c) {
+  if (c->have_RL) return;
+  const int n = c->npairs;
+  const size_t nn = (size_t)n * n;
+  c->MR.ensure(sizeof(double2) * nn);
+  c->ML.ensure(sizeof(double2) * nn);
+  c->Rm.ensure(sizeof(double2) * nn);
+  c->Lm.ensure(sizeof(double2) * nn);
+  c->Wm.ensure(sizeof(double2) * nn);
+  gram_work_ensure(c, nn * 4);
+  ProfScope ps(c, SWI_K_PROJ, 2.0 * 8.0 * c->N * (double)n * n, 2.0 * 16.0 * c->N * (double)n + 16.0 * c->N);
+  swi::GramBatch gb;
+  gb.n = 1;
+  gb.job[0] = swi::GramJob{c->U.as<double2>(), c->U.as<double2>(), c->MR.as<double2>(), n, n, n, n, n, 0};
+  swi::launch_gram(gb, c->N, c->gR.as<double>(), 0, c->gram_work.as<double2>(), c->gram_work.bytes / sizeof(double2),
+                   c->stream, &c->launches);
+  gb.job[0].C = c->ML.as<double2>();
+  swi::launch_gram(gb, c->N, c->gL.as<double>(), 0, c->gram_work.as<double2>(), c->gram_work.bytes / sizeof(double2),
+                   c->stream, &c->launches);
+  swi::launch_wbuild(c->MR.as<double2>(), c->ML.as<double2>(), n, c->Rm.as<double2>(), c->Lm.as<double2>(),
+                     c->Wm.as<double2>(), c->stream, &c->launches);
+  c->have_RL = true;
+}
+
+bool finite_all(const double* p, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(p[i])) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+swi_status swi_create(swi_ctx** out, int nx, int ny, int nz, double h, int bc, int precision, void* cuda_stream) {
+  if (!out) return fail(nullptr, SWI_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (nx < 6 || ny < 6 || nz < 6) return fail(nullptr, SWI_EINVAL, "each axis needs at least 6 points");
+  if (!(h > 0.0) || !std::isfinite(h)) return fail(nullptr, SWI_EINVAL, "grid spacing must be positive");
+  if (bc != SWI_BC_ODD && bc != SWI_BC_ZERO) return fail(nullptr, SWI_EINVAL, "unknown boundary rule");
+  if (precision != SWI_PREC_F64)
+    return fail(nullptr, precision == SWI_PREC_MIXED ? SWI_ENOTIMPL : SWI_EINVAL, "only SWI_PREC_F64 is available");
+  const long long N = (long long)nx * ny * nz;
+  if (N > (1LL << 31) - 1) return fail(nullptr, SWI_EINVAL, "grid too large");
+  swi_ctx* c = nullptr;
+  try {
+    c = new swi_ctx();
+  } catch (...) {
+    return fail(nullptr, SWI_ENOMEM, "host allocation failed");
+  }
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return fail(nullptr, SWI_ECUDA, "no CUDA device");
+  }
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  c->nx = nx;
+  c->ny = ny;
+  c->nz = nz;
+  c->N = (int)N;
+  c->h = h;
+  c->bc = bc;
+  c->precision = precision;
+  *out = c;
+  return SWI_OK;
+}
+
+swi_status swi_set_potential(swi_ctx* c, const double* V, int on_device) {
+  return guarded(c, [&]() -> swi_status {
+    if (!V) return fail(c, SWI_EINVAL, "V is NULL");
+    const size_t n = c->N;
+    std::vector<double> h(n);
+    if (on_device) {
+      SWI_CUDA_TRY(cudaMemcpy(h.data(), V, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    } else {
+      std::memcpy(h.data(), V, sizeof(double) * n);
+    }
+    if (!finite_all(h.data(), n)) return fail(c, SWI_EINVAL, "V has a non-finite value");
+    double mx = 0.0;
+    for (double v : h) mx = std::max(mx, std::fabs(v));
+    copy_in(c->V, h.data(), sizeof(double) * n, false, c->stream);
+    sync(c->stream);
+    c->maxabsV = mx;
+    c->has_V = true;
+    return SWI_OK;
+  });
+}
+
+swi_status swi_set_absorber(swi_ctx* c, const double* gL, const double* gR, int on_device) {
+  return guarded(c, [&]() -> swi_status {
+    if (!gL || !gR) return fail(c, SWI_EINVAL, "absorber is NULL");
+    const size_t n = c->N;
+    std::vector<double> l(n), r(n), g(n);
+    if (on_device) {
+      SWI_CUDA_TRY(cudaMemcpy(l.data(), gL, sizeof(double) * n, cudaMemcpyDeviceToHost));
+      SWI_CUDA_TRY(cudaMemcpy(r.data(), gR, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    } else {
+      std::memcpy(l.data(), gL, sizeof(double) * n);
+      std::memcpy(r.data(), gR, sizeof(double) * n);
+    }
+    double mx = 0.0;
+    for (size_t i = 0; i < n; ++i) {
+      if (!std::isfinite(l[i]) || !std::isfinite(r[i]) || l[i] < 0.0 || r[i] < 0.0)
+        return fail(c, SWI_EINVAL, "absorbers must be finite and non-negative");
+      g[i] = l[i] + r[i];
+      mx = std::max(mx, g[i]);
+    }
+    copy_in(c->gL, l.data(), sizeof(double) * n, false, c->stream);
+    copy_in(c->gR, r.data(), sizeof(double) * n, false, c->stream);
+    copy_in(c->G, g.data(), sizeof(double) * n, false, c->stream);
+    sync(c->stream);
+    c->maxG = mx;
+    c->has_G = true;
+    c->have_RL = false;
+    return SWI_OK;
+  });
+}
+
+swi_status swi_set_windows(swi_ctx* c, int p, const double* sigma, const int* n_req) {
+  return guarded(c, [&]() -> swi_status {
+    if (p < 1 || !sigma || !n_req) return fail(c, SWI_EINVAL, "need p >= 1 windows");
+    if (p > swi::kMaxBatch) return fail(c, SWI_EINVAL, "at most 64 windows");
+    for (int j = 0; j < p; ++j) {
+      if (!std::isfinite(sigma[j])) return fail(c, SWI_EINVAL, "non-finite shift");
+      if (n_req[j] < 1) return fail(c, SWI_EINVAL, "each window needs n_req >= 1");
+      if (j > 0 && !(sigma[j] > sigma[j - 1])) return fail(c, SWI_EINVAL, "shifts must be strictly increasing");
+    }
+    c->sigma.assign(sigma, sigma + p);
+    c->nreq.assign(n_req, n_req + p);
+    return SWI_OK;
+  });
+}
+
+swi_status swi_plan_windows(swi_ctx* c, int n_r, int p, double e_min, double e_max, double inflate,
+                            double* sigma_out, int* n_req_out) {
+  return guarded(c, [&]() -> swi_status {
+    if (n_r < 1 || p < 1 || p > swi::kMaxBatch) return fail(c, SWI_EINVAL, "need n_r >= 1 and 1 <= p <= 64");
+    if (!(e_max > e_min)) return fail(c, SWI_EINVAL, "need e_max > e_min");
+    if (!(inflate >= 1.0)) inflate = 1.0;
+    // Algorithm 1: n_r,j (round / ceil heuristics), then E_S,j
+    std::vector<long long> cnt(p + 1, 0);
+    for (int j = 1; j <= p; ++j) {
+      if (j <= p / 2.0) {
+        const double x = 2.0 / (1.5 + (double)(j - 1) / p) * (double)n_r / p;
+        cnt[j] = (long long)std::floor(x + 0.5);
+      } else {
+        cnt[j] = (long long)std::ceil(2.0 * n_r / p) - cnt[p - j + 1];
+      }
+    }
+    std::vector<double> sg(p);
+    std::vector<int> rq(p);
+    const double step = (e_max - e_min) / c->N;
+    double prev_s = e_min;
+    long long prev_n = 0;
+    for (int j = 1; j <= p; ++j) {
+      const double s = prev_s + step * (double)(cnt[j] + prev_n) / 2.0;
+      sg[j - 1] = s;
+      rq[j - 1] = (int)std::max(1LL, (long long)std::ceil(cnt[j] * inflate));
+      prev_s = s;
+      prev_n = cnt[j];
+    }
+    for (int j = 1; j < p; ++j)
+      if (!(sg[j] > sg[j - 1])) return fail(c, SWI_EINVAL, "plan produced non-increasing shifts");
+    if (sigma_out) std::copy(sg.begin(), sg.end(), sigma_out);
+    if (n_req_out) std::copy(rq.begin(), rq.end(), n_req_out);
+    c->sigma = sg;
+    c->nreq = rq;
+    return SWI_OK;
+  });
+}
+
+swi_status swi_apply(swi_ctx* c, int nvec, const double* sigma, const void* X, void* Y, int on_device) {
+  return guarded(c, [&]() -> swi_status {
+    if (nvec < 1 || !sigma || !X || !Y) return fail(c, SWI_EINVAL, "bad arguments");
+    if (!c->has_V || !c->has_G) return fail(c, SWI_ESTATE, "potential and absorbers must be set");
+    const size_t bytes = sizeof(double2) * (size_t)c->N * nvec;
+    c->sig_dev.ensure(sizeof(double) * std::max(nvec, 64));
+    SWI_CUDA_TRY(cudaMemcpyAsync(c->sig_dev.p, sigma, sizeof(double) * nvec, cudaMemcpyHostToDevice, c->stream));
+    if (on_device) {
+      apply_block(c, static_cast<const double2*>(X), nvec, static_cast<double2*>(Y), nvec, nvec);
+      sync(c->stream);
+      return SWI_OK;
+    }
+    DevMem dx, dy;
+    dx.ensure(bytes);
+    dy.ensure(bytes);
+    SWI_CUDA_TRY(cudaMemcpyAsync(dx.p, X, bytes, cudaMemcpyHostToDevice, c->stream));
+    apply_block(c, dx.as<double2>(), nvec, dy.as<double2>(), nvec, nvec);
+    SWI_CUDA_TRY(cudaMemcpyAsync(Y, dy.p, bytes, cudaMemcpyDeviceToHost, c->stream));
+    sync(c->stream);
+    return SWI_OK;
+  });
+}
+
+swi_status swi_solve(swi_ctx* c, const swi_solve_opts* opts, swi_solve_info* info) {
+  return guarded(c, [&]() -> swi_status { return do_solve(c, opts, info); });
+}
+
+swi_status swi_get_window_info(swi_ctx* c, int cap, swi_window_info* out, int* p) {
+  return guarded(c, [&]() -> swi_status {
+    if (p) *p = (int)c->winfo.size();
+    if (out)
+      for (int j = 0; j < cap && j < (int)c->winfo.size(); ++j) out[j] = c->winfo[j];
+    return SWI_OK;
+  });
+}
+
+swi_status swi_get_eigenpairs(swi_ctx* c, int* n, const void** eps_dev, const void** U_dev, int* ldU) {
+  return guarded(c, [&]() -> swi_status {
+    if (c->npairs <= 0) return fail(c, SWI_ESTATE, "no eigenpairs: call swi_solve first");
+    if (n) *n = c->npairs;
+    if (eps_dev) *eps_dev = c->eps.p;
+    if (U_dev) *U_dev = c->U.p;
+    if (ldU) *ldU = c->npairs;
+    return SWI_OK;
+  });
+}
+
+swi_status swi_copy_eigenpairs(swi_ctx* c, void* eps, void* U, int on_device) {
+  return guarded(c, [&]() -> swi_status {
+    if (c->npairs <= 0) return fail(c, SWI_ESTATE, "no eigenpairs: call swi_solve first");
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (eps) SWI_CUDA_TRY(cudaMemcpyAsync(eps, c->eps.p, sizeof(double2) * c->npairs, k, c->stream));
+    if (U) SWI_CUDA_TRY(cudaMemcpyAsync(U, c->U.p, sizeof(double2) * (size_t)c->N * c->npairs, k, c->stream));
+    sync(c->stream);
+    return SWI_OK;
+  });
+}
+
+swi_status swi_set_eigenpairs(swi_ctx* c, int n, const void* eps, const void* U, int on_device) {
+  return guarded(c, [&]() -> swi_status {
+    if (n < 1 || !eps || !U) return fail(c, SWI_EINVAL, "bad arguments");
+    copy_in(c->eps, eps, sizeof(double2) * n, on_device != 0, c->stream);
+    copy_in(c->U, U, sizeof(double2) * (size_t)c->N * n, on_device != 0, c->stream);
+    sync(c->stream);
+    c->npairs = n;
+    c->have_RL = false;
+    c->resid.clear();
+    return SWI_OK;
+  });
+}
+
+swi_status swi_residuals(swi_ctx* c, double* res_out) {
+  return guarded(c, [&]() -> swi_status {
+    if (c->npairs <= 0) return fail(c, SWI_ESTATE, "no eigenpairs");
+    if (!c->has_V || !c->has_G) return fail(c, SWI_ESTATE, "potential and absorbers must be set");
+    if (!res_out) return fail(c, SWI_EINVAL, "res_out is NULL");
+    std::vector<double> r;
+    explicit_residuals(c, c->U.as<double2>(), c->npairs, c->eps.as<double2>(), c->npairs, r);
+    std::copy(r.begin(), r.end(), res_out);
+    return SWI_OK;
+  });
+}
+
+swi_status swi_transmission(swi_ctx* c, int nE, const double* E, double* T_out) {
+  return guarded(c, [&]() -> swi_status {
+    if (c->npairs <= 0) return fail(c, SWI_ESTATE, "no eigenpairs");
+    if (!c->has_G) return fail(c, SWI_ESTATE, "absorbers must be set");
+    if (nE < 1 || !E || !T_out) return fail(c, SWI_EINVAL, "bad arguments");
+    if (!finite_all(E, nE)) return fail(c, SWI_EINVAL, "non-finite energy");
+    ensure_RL(c);
+    copy_in(c->Ebuf, E, sizeof(double) * nE, false, c->stream);
+    c->Tbuf.ensure(sizeof(double) * nE);
+    {
+      const double nn = (double)c->npairs * c->npairs;
+      ProfScope ps(c, SWI_K_TRANS, 8.0 * nE * nn, 16.0 * nn);
+      swi::launch_transmission(c->Wm.as<double2>(), c->eps.as<double2>(), c->npairs, c->Ebuf.as<double>(), nE,
+                               c->Tbuf.as<double>(), nullptr, c->stream, &c->launches);
+    }
+    SWI_CUDA_TRY(cudaMemcpyAsync(T_out, c->Tbuf.p, sizeof(double) * nE, cudaMemcpyDeviceToHost, c->stream));
+    sync(c->stream);
+    return SWI_OK;
+  });
+}
+
+swi_status swi_grad(swi_ctx* c, int nE, const double* E, const double* dLdT, double* dLdV, int dLdV_on_device,
+                    double* dTdE) {
+  return guarded(c, [&]() -> swi_status {
+    if (c->npairs <= 0) return fail(c, SWI_ESTATE, "no eigenpairs");
+    if (!c->has_G) return fail(c, SWI_ESTATE, "absorbers must be set");
+    if (nE < 1 || !E) return fail(c, SWI_EINVAL, "bad arguments");
+    if (dLdV && !dLdT) return fail(c, SWI_EINVAL, "dLdV needs dLdT");
+    if (!finite_all(E, nE) || (dLdT && !finite_all(dLdT, nE))) return fail(c, SWI_EINVAL, "non-finite input");
+    ensure_RL(c);
+    const int n = c->npairs;
+    copy_in(c->Ebuf, E, sizeof(double) * nE, false, c->stream);
+    if (dTdE) {
+      c->Tbuf.ensure(sizeof(double) * nE);
+      c->dEbuf.ensure(sizeof(double) * nE);
+      ProfScope ps(c, SWI_K_TRANS, 8.0 * nE * (double)n * n, 16.0 * (double)n * n);
+      swi::launch_transmission(c->Wm.as<double2>(), c->eps.as<double2>(), n, c->Ebuf.as<double>(), nE,
+                               c->Tbuf.as<double>(), c->dEbuf.as<double>(), c->stream, &c->launches);
+      SWI_CUDA_TRY(cudaMemcpyAsync(dTdE, c->dEbuf.p, sizeof(double) * nE, cudaMemcpyDeviceToHost, c->stream));
+    }
+    if (dLdV) {
+      copy_in(c->wbuf, dLdT, sizeof(double) * nE, false, c->stream);
+      c->Mg.ensure(sizeof(double2) * (size_t)n * n);
+      ProfScope ps(c, SWI_K_GRAD, 8.0 * (double)n * n * ((double)nE * n + c->N),
+                   16.0 * c->N * (double)n * 2.0 + 8.0 * c->N);
+      swi::launch_gradM(c->Rm.as<double2>(), c->Lm.as<double2>(), c->eps.as<double2>(), n, c->Ebuf.as<double>(),
+                        c->wbuf.as<double>(), nE, c->Mg.as<double2>(), c->stream, &c->launches);
+      c->scratch.ensure(sizeof(double2) * (size_t)c->N * n);
+      swi::RowGemmBatch rb;
+      rb.n = 1;
+      rb.job[0] = swi::RowGemmJob{c->U.as<double2>(), c->Mg.as<double2>(), nullptr, c->scratch.as<double2>(), n, n, 0,
+                                  n, n, n, 1.0, 0.0};
+      swi::launch_rowgemm(rb, c->N, c->stream, &c->launches);
+      DevMem tmp;
+      double* dst = dLdV;
+      if (!dLdV_on_device) {
+        tmp.ensure(sizeof(double) * c->N);
+        dst = tmp.as<double>();
+      }
+      swi::launch_rowdot(c->scratch.as<double2>(), n, c->U.as<double2>(), n, n, c->N, dst, c->stream, &c->launches);
+      if (!dLdV_on_device)
+        SWI_CUDA_TRY(cudaMemcpyAsync(dLdV, dst, sizeof(double) * c->N, cudaMemcpyDeviceToHost, c->stream));
+      sync(c->stream);
+    }
+    sync(c->stream);
+    return SWI_OK;
+  });
+}
+
+swi_status swi_profile(swi_ctx* c, int enable) {
+  return guarded(c, [&]() -> swi_status {
+    sync(c->stream);
+    for (auto& r : c->prof) {
+      c->evpool.push_back(r.a);
+      c->evpool.push_back(r.b);
+    }
+    c->prof.clear();
+    c->prof_on = enable != 0;
+    return SWI_OK;
+  });
+}
+
+swi_status swi_profile_read(swi_ctx* c, swi_kernel_stats* out) {
+  return guarded(c, [&]() -> swi_status {
+    if (!out) return fail(c, SWI_EINVAL, "out is NULL");
+    sync(c->stream);
+    for (int k = 0; k < SWI_K_COUNT; ++k) out[k] = swi_kernel_stats{0, 0.0, 0.0, 0.0};
+    for (auto& r : c->prof) {
+      float ms = 0.f;
+      SWI_CUDA_TRY(cudaEventElapsedTime(&ms, r.a, r.b));
+      swi_kernel_stats& s = out[r.kind];
+      s.launches += 1;
+      s.ms += ms;
+      s.flops += r.flops;
+      s.bytes += r.bytes;
+    }
+    return SWI_OK;
+  });
+}
+
+const char* swi_last_error(const swi_ctx* c) {
+  if (!c) return g_create_error.c_str();
+  return c->err.c_str();
+}
+
+long long swi_launch_count(const swi_ctx* c) { return c ? c->launches : 0; }
+
+void swi_destroy(swi_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  delete c;
+}
+
+}  // extern "C"

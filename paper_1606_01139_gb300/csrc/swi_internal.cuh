@@ -1,0 +1,235 @@
+// Internal declarations shared by the translation units of the library.
+// Complex values are double2 (x = re, y = im); blocks of vectors are row-major
+// [N][ld] with the vector index innermost.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/swi.h"
+
+namespace swi {
+
+// ---------------------------------------------------------------- complex math
+__host__ __device__ __forceinline__ double2 cmk(double r, double i) { return make_double2(r, i); }
+__host__ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+__host__ __device__ __forceinline__ double2 cmulc(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -a.x * b.y));
+}
+__host__ __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__host__ __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+// acc += a * b
+__host__ __device__ __forceinline__ void cfma(double2& acc, double2 a, double2 b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+}
+// acc += conj(a) * b
+__host__ __device__ __forceinline__ void cfmac(double2& acc, double2 a, double2 b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(-a.y, b.x, acc.y);
+}
+__host__ __device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+__host__ __device__ __forceinline__ double cabs(double2 a) { return hypot(a.x, a.y); }
+__host__ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+  // Smith's algorithm
+  if (fabs(b.x) >= fabs(b.y)) {
+    double r = b.y / b.x, d = b.x + b.y * r;
+    return make_double2((a.x + a.y * r) / d, (a.y - a.x * r) / d);
+  } else {
+    double r = b.x / b.y, d = b.y + b.x * r;
+    return make_double2((a.x * r + a.y) / d, (a.y * r - a.x) / d);
+  }
+}
+// principal square root
+__host__ __device__ __forceinline__ double2 csqrt_p(double2 z) {
+  double r = hypot(z.x, z.y);
+  if (r == 0.0) return make_double2(0.0, 0.0);
+  double t = sqrt(0.5 * (r + fabs(z.x)));
+  if (z.x >= 0.0) return make_double2(t, z.y / (2.0 * t));
+  return make_double2(fabs(z.y) / (2.0 * t), copysign(t, z.y));
+}
+
+// ---------------------------------------------------------------- error plumbing
+struct Error {
+  swi_status code;
+  std::string msg;
+};
+
+#define SWI_CUDA_TRY(call)                                                                \
+  do {                                                                                    \
+    cudaError_t e__ = (call);                                                             \
+    if (e__ != cudaSuccess)                                                               \
+      throw ::swi::Error{SWI_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e__)}; \
+  } while (0)
+
+#define SWI_CHECK_LAUNCH() SWI_CUDA_TRY(cudaGetLastError())
+
+// ---------------------------------------------------------------- operator data
+struct StencilParams {
+  int nx, ny, nz;
+  int bc;             // SWI_BC_ODD or SWI_BC_ZERO
+  double cm[7];       // -c_m / (2 h^2), m = 0..6 (centre weight counts once per axis)
+  const double* V;    // N
+  const double* G;    // Gamma_L + Gamma_R, N
+};
+
+// One block of columns for the batched stencil: Y[:, c] = (A - sigma[c]) X[:, c]
+struct StencilBlock {
+  const double2* X;
+  double2* Y;
+  int ldx, ldy, ncols;
+  int sigma_off;      // index into the sigma table of column 0
+};
+
+constexpr int kMaxBatch = 64;
+
+struct StencilBatch {
+  int n;
+  StencilBlock blk[kMaxBatch];
+};
+
+void launch_stencil(const StencilParams& P, const StencilBatch& batch, const double* sigma_dev,
+                    cudaStream_t s, long long* launches);
+
+// ---------------------------------------------------------------- tall-skinny products
+// C_j = op(X_j)^H diag(w) Y_j over the N rows (op = conj for the Hermitian
+// product, identity-conjugate for the bilinear one), reduced deterministically.
+struct GramJob {
+  const double2* X;  // [N][ldx], columns [0, nx)
+  const double2* Y;  // [N][ldy], columns [0, ny)
+  double2* C;        // [nx][ldc] result (row i = column i of X)
+  int ldx, ldy, ldc, nx, ny;
+  int accumulate;    // C += result instead of C = result
+};
+struct GramBatch {
+  int n;
+  GramJob job[kMaxBatch];
+};
+// bilinear != 0: C = X^T diag(w) Y; else C = X^H diag(w) Y.  w may be NULL.
+void launch_gram(const GramBatch& b, int N, const double* w, int bilinear, double2* work,
+                 size_t work_elems, cudaStream_t s, long long* launches);
+
+// Out[n, 0:ncols] = beta * Yin[n, 0:ncols] + alpha * X[n, 0:k] * M[0:k, 0:ncols]  (M is [k][ldm])
+struct RowGemmJob {
+  const double2* X;    // [N][ldx]
+  const double2* M;    // [k][ldm] (device)
+  const double2* Yin;  // [N][ldy] or NULL (beta ignored)
+  double2* Out;        // [N][ldo]
+  int ldx, ldm, ldy, ldo, k, ncols;
+  double alpha, beta;
+};
+struct RowGemmBatch {
+  int n;
+  RowGemmJob job[kMaxBatch];
+};
+void launch_rowgemm(const RowGemmBatch& b, int N, cudaStream_t s, long long* launches);
+
+// Per-column 2-norms of a residual block R = Y - X diag(theta): out[c] = ||Y[:,c] - theta_c X[:,c]||.
+void launch_colnorm_resid(const double2* X, int ldx, const double2* Y, int ldy, const double2* theta,
+                          int ncols, int N, double* out, double* work, size_t work_elems,
+                          cudaStream_t s, long long* launches);
+
+// Fill [N][ld] columns [c0, c0+ncols) with counter-based pseudo-random complex numbers.
+void launch_random_block(double2* X, int ld, int c0, int ncols, int N, unsigned long long seed,
+                         cudaStream_t s, long long* launches);
+
+// ---------------------------------------------------------------- small dense (per window)
+// Cholesky of Hermitian G (b x b, ld b) -> upper R with G = R^H R, and Rinv = R^{-1}.
+// status[j] set to 1 if G is not numerically positive definite.
+struct CholBatch {
+  int n;
+  const double2* G[kMaxBatch];
+  double2* R[kMaxBatch];
+  double2* Rinv[kMaxBatch];
+};
+void launch_chol_batch(const CholBatch& cb, int b, int* status, cudaStream_t s, long long* launches);
+
+struct SchurJob {
+  double2* H;        // [m][ld] in/out: on exit, T (upper triangular Schur form)
+  double2* Z;        // [m][ld] out: unitary Schur vectors (column i = vector i)
+  const double2* B;  // [b][ld] coupling rows (residual relation)
+  double2* Bz;       // [b][ld] out: B Z[:, 0:k]
+  double2* theta;    // [m] out: diag(T) after reordering
+  double* resid;     // [m] out: ||B Z s_i|| / ||s_i|| for the kept Ritz vectors
+  double2* S;        // [m][ld] out: eigenvectors of T[0:k,0:k] (columns), unit 2-norm
+  int* ordinfo;      // [4]: out k (kept), nwanted_conv, status
+  int m, ld, b, keep, nwant;
+  int kmax;         // the kept block is never extended beyond kmax columns
+  double tol_abs;    // absolute residual threshold
+};
+struct SchurBatch {
+  int n;
+  SchurJob job[kMaxBatch];
+};
+void launch_schur_batch(const SchurBatch& b, cudaStream_t s, long long* launches);
+
+// Ritz coefficient matrix of the wanted pairs after a Schur step:
+// Yw[:, q] = Z[:, 0:k] s_{w_q} (m x nwant, [m][ld]) and eps_w[q] = theta_{w_q} + sigma,
+// wanted = the nwant smallest |theta| of the leading k, ordered by (Re, Im).
+struct RitzJob {
+  const double2* Z;
+  const double2* S;
+  const double2* theta;
+  const double* resid;
+  const int* ordinfo;
+  double2* Yw;       // [m][ldy]
+  double2* eps;      // [nwant]
+  double* res_out;   // [nwant]
+  int m, ld, ldy, nwant;
+  double sigma;
+};
+struct RitzBatch {
+  int n;
+  RitzJob job[kMaxBatch];
+};
+void launch_ritz_batch(const RitzBatch& b, cudaStream_t s, long long* launches);
+
+// Block-Arnoldi bookkeeping after one expansion (A [Q V] = [Q V] H' + V' B'):
+// H[0:p+b, p:p+b] = C1 + C2, H[p:p+b, 0:p] = B_old[:, 0:p], B = [0, R2 R1].
+struct HUpdJob {
+  double2* H;          // [ld][ld]
+  double2* Bm;         // [b][ld]
+  const double2* C1;   // [p+b][b]
+  const double2* C2;   // [p+b][b]
+  const double2* R1;   // [b][b]
+  const double2* R2;   // [b][b]
+  int ld, p, b;
+};
+struct HUpdBatch {
+  int n;
+  HUpdJob job[kMaxBatch];
+};
+void launch_hupdate_batch(const HUpdBatch& b, cudaStream_t s, long long* launches);
+
+// Zext = [[Z[:, 0:k], 0], [0, I_b]]  ((m+b) x (k+b), [m+b][ldo]) for the thick restart.
+struct ZextJob {
+  const double2* Z;
+  double2* Zext;
+  int ldz, ldo, m, k, b;
+};
+struct ZextBatch {
+  int n;
+  ZextJob job[kMaxBatch];
+};
+void launch_zext_batch(const ZextBatch& b, cudaStream_t s, long long* launches);
+
+// small element-wise helpers
+void launch_copy_block(const double2* src, int lds, double2* dst, int ldd, int rows, int cols,
+                       cudaStream_t s, long long* launches);
+
+// ---------------------------------------------------------------- timing helper
+double now_seconds();
+
+}  // namespace swi

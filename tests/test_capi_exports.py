@@ -1,0 +1,62 @@
+"""The C-ABI library builds, loads, and exports every entry point include/swi.h declares.
+
+No compute call is made here (no GPU on the CPU runner)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+
+
+def _declared():
+    with open(os.path.join(ROOT, "include", "swi.h")) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(swi_[a-z_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1606_01139_gb300 import build as b
+    path = b.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_call_list():
+    d = _declared()
+    for name in ("swi_create", "swi_set_potential", "swi_set_absorber", "swi_set_windows", "swi_solve",
+                 "swi_transmission", "swi_grad", "swi_last_error", "swi_destroy"):
+        assert name in d
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_export_list_matches_header():
+    import paper_1606_01139_gb300 as swi
+    assert sorted(swi.EXPORTS) == _declared()
+
+
+def test_binding_fails_loudly_without_library(tmp_path):
+    import paper_1606_01139_gb300 as swi
+    saved = swi._lib
+    try:
+        swi._lib = None
+        with pytest.raises(RuntimeError):
+            swi.load(str(tmp_path / "missing.so"))
+    finally:
+        swi._lib = saved
+
+
+def test_create_without_device_reports_an_error(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a device is present")
+    import paper_1606_01139_gb300 as swi
+    swi.load()
+    with pytest.raises(swi.SwiError):
+        swi.Context(10, 10, 20, 0.5, stream=0)

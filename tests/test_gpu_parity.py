@@ -1,0 +1,256 @@
+"""GPU path (through the C ABI) against the CPU oracle, element by element.
+
+Tolerances (FP64 path): stencil outputs within 1e-13 of the output scale
+(rounding order only); eigenvalues within 1e-10 max(1, |eps|); U^T U = I
+within 1e-10; relative residuals below the requested 1e-11; T(E) and its
+gradients within 1e-9 relative of the oracle evaluated on its own dense
+eigenpairs.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import eigen, partition, stencil, transport
+
+pytestmark = pytest.mark.gpu
+
+EPS_TOL = 1e-10
+REL_TOL = 1e-11
+
+
+@pytest.fixture(scope="module")
+def swi():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import paper_1606_01139_gb300 as lib
+    from paper_1606_01139_gb300 import build as b
+    b.build()
+    lib.load()
+    return lib
+
+
+def _ctx(swi, w, bc=0):
+    c = swi.Context(w.nx, w.ny, w.nz, w.h, bc=bc)
+    c.set_potential(w.V)
+    c.set_absorber(w.gamma_L, w.gamma_R)
+    return c
+
+
+def _dense(w, bc=0):
+    return stencil.dense_A(w.nx, w.ny, w.nz, w.h, w.V, w.gamma_L, w.gamma_R, bc=bc)
+
+
+def _eps_err(a, b):
+    return np.max(np.abs(a - b) / np.maximum(1.0, np.abs(b)))
+
+
+# --------------------------------------------------------------------------- stencil
+@pytest.mark.parametrize("shape", [(13, 11, 14), (6, 7, 9), (20, 17, 31)])
+@pytest.mark.parametrize("bc", [0, 1])
+def test_stencil_parity_ragged(swi, shape, bc):
+    w = W.make_wire(*shape, 0.5, 4, 3)
+    rng = np.random.default_rng(1)
+    nvec = 7
+    X = rng.standard_normal((w.N, nvec)) + 1j * rng.standard_normal((w.N, nvec))
+    sig = rng.uniform(-2, 2, nvec)
+    with _ctx(swi, w, bc) as c:
+        Y = c.apply(X, sig)
+    Yo = stencil.apply_A(X, w.nx, w.ny, w.nz, w.h, w.V, w.gamma_L, w.gamma_R, bc=bc) - X * sig[None, :]
+    assert np.max(np.abs(Y - Yo)) <= 1e-13 * np.max(np.abs(Yo))
+
+
+def test_stencil_parity_full_size_block16(swi):
+    # the 48x48x96 workload in the launch shape of the Krylov loop (block of 16)
+    w = W.config_wire("wire_48x48x96")
+    rng = np.random.default_rng(2)
+    X = rng.standard_normal((w.N, 16)) + 1j * rng.standard_normal((w.N, 16))
+    sig = np.linspace(-1.0, 0.5, 16)
+    with _ctx(swi, w) as c:
+        Y = c.apply(X, sig)
+    Yo = stencil.apply_A(X, w.nx, w.ny, w.nz, w.h, w.V, w.gamma_L, w.gamma_R) - X * sig[None, :]
+    assert np.max(np.abs(Y - Yo)) <= 1e-13 * np.max(np.abs(Yo))
+
+
+def test_stencil_device_pointers(swi):
+    import torch
+    w = W.make_wire(9, 8, 10, 0.5, 2, 5)
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((w.N, 3)) + 1j * rng.standard_normal((w.N, 3))
+    with _ctx(swi, w) as c:
+        Yd = c.apply(torch.as_tensor(X).cuda(), np.zeros(3))
+        Yh = c.apply(X, np.zeros(3))
+    assert np.array_equal(Yd.cpu().numpy(), Yh)
+
+
+# --------------------------------------------------------------------------- solve
+def _solve_vs_dense(swi, w, n_r, p, block, inflate=1.3, extra=4):
+    A = _dense(w)
+    eps_o, U_o = eigen.dense_spectrum(A)
+    # the selection boundary must not split a degenerate cluster
+    assert abs(eps_o[n_r] - eps_o[n_r - 1]) > 1e-6
+    sig, req = W.count_windows(eps_o.real[:n_r], partition.window_counts(n_r, p), inflate=inflate, extra=extra)
+    with _ctx(swi, w) as c:
+        c.set_windows(sig, req)
+        info = c.solve(block=block, rel_tol=REL_TOL, n_keep=n_r, max_matvecs=60000)
+        eps, U = c.eigenpairs()
+        res = c.residuals()
+        winfo = c.window_info()
+    return A, eps_o, U_o, eps, U, res, info, winfo
+
+
+def _check_pairs(w, eps_o, U_o, eps, U, res, info, n_r):
+    assert info["status"] == "SWI_OK", info
+    assert len(eps) == n_r
+    assert _eps_err(eps, eps_o[:n_r]) <= EPS_TOL
+    assert np.max(res) <= REL_TOL
+    np.testing.assert_allclose(U.T @ U, np.eye(n_r), atol=1e-10)
+    g = w.gamma_L + w.gamma_R
+    assert np.all(eps.imag <= 1e-12) and np.all(-eps.imag <= g.max() + 1e-12)
+    for cl in eigen.clusters(eps_o[:n_r], 1e-9):
+        P = eigen.cluster_projector(U, cl)
+        Po = eigen.cluster_projector(U_o, cl)
+        assert np.max(np.abs(P - Po)) <= 1e-8 * max(1.0, np.max(np.abs(Po)))
+
+
+def test_solve_small_two_windows(swi):
+    w = W.make_wire(8, 8, 14, 0.5, 4, 1)
+    A, eps_o, U_o, eps, U, res, info, winfo = _solve_vs_dense(swi, w, 16, 2, block=4)
+    _check_pairs(w, eps_o, U_o, eps, U, res, info, 16)
+    assert info["n_duplicates"] > 0 and info["n_holes"] == 0
+
+
+def test_solve_ragged_grid_three_windows(swi):
+    w = W.make_wire(11, 9, 17, 0.5, 5, 7)
+    A, eps_o, U_o, eps, U, res, info, winfo = _solve_vs_dense(swi, w, 20, 3, block=8)
+    _check_pairs(w, eps_o, U_o, eps, U, res, info, 20)
+
+
+@pytest.fixture(scope="module")
+def wire10(swi):
+    w = W.config_wire("wire_10x10x20")
+    return (w,) + _solve_vs_dense(swi, w, 48, 4, block=8)
+
+
+def test_wire_10x10x20_eigenpairs(wire10):
+    w, A, eps_o, U_o, eps, U, res, info, winfo = wire10
+    _check_pairs(w, eps_o, U_o, eps, U, res, info, 48)
+
+
+def test_wire_10x10x20_transmission_and_gradients(swi, wire10):
+    w, A, eps_o, U_o, eps, U, res, info, winfo = wire10
+    E = W.energy_grid(eps_o.real[0], eps_o.real[47], 32)
+    To = transport.transmission_spectral(eps_o[:48], U_o[:, :48], w.gamma_L, w.gamma_R, E)
+    dEo = transport.grad_E_spectral(eps_o[:48], U_o[:, :48], w.gamma_L, w.gamma_R, E)
+    wts = np.random.default_rng(4).standard_normal(len(E))
+    dVo = transport.grad_V_spectral(eps_o[:48], U_o[:, :48], w.gamma_L, w.gamma_R, E, wts)
+    with _ctx(swi, w) as c:
+        c.set_eigenpairs(eps, U)
+        T = c.transmission(E)
+        dV, dE = c.grad(E, wts)
+    assert np.max(np.abs(T - To)) <= 1e-9 * max(1.0, np.max(np.abs(To)))
+    assert np.max(np.abs(dE - dEo)) <= 1e-9 * max(1.0, np.max(np.abs(dEo)))
+    assert np.max(np.abs(dV - dVo)) <= 1e-9 * max(1.0, np.max(np.abs(dVo)))
+
+
+def test_transport_kernels_on_oracle_pairs(swi):
+    # T(E), dT/dE and dL/dV from the oracle's own eigenpairs: isolates the kernels.
+    w = W.make_wire(7, 6, 12, 0.5, 3, 9)
+    A = _dense(w)
+    eps_o, U_o = eigen.dense_spectrum(A)
+    n = 60
+    E = np.linspace(eps_o.real[0] - 0.2, eps_o.real[n - 1], 9)
+    wts = np.random.default_rng(5).standard_normal(len(E))
+    To = transport.transmission_spectral(eps_o[:n], U_o[:, :n], w.gamma_L, w.gamma_R, E)
+    dEo = transport.grad_E_spectral(eps_o[:n], U_o[:, :n], w.gamma_L, w.gamma_R, E)
+    dVo = transport.grad_V_spectral(eps_o[:n], U_o[:, :n], w.gamma_L, w.gamma_R, E, wts)
+    with _ctx(swi, w) as c:
+        c.set_eigenpairs(eps_o[:n], U_o[:, :n])
+        T = c.transmission(E)
+        dV, dE = c.grad(E, wts)
+    np.testing.assert_allclose(T, To, rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(dE, dEo, rtol=1e-11, atol=1e-13 * np.max(np.abs(dEo)))
+    np.testing.assert_allclose(dV, dVo, rtol=1e-11, atol=1e-13 * np.max(np.abs(dVo)))
+
+
+def test_full_spectrum_transmission_equals_direct_inverse(swi):
+    # With all N pairs the spectral G is the inverse: GPU T(E) = oracle dense-inverse T(E).
+    w = W.make_wire(6, 6, 8, 0.5, 2, 4)
+    A = _dense(w)
+    eps_o, U_o = eigen.dense_spectrum(A)
+    E = np.array([-0.3, 0.4, 1.2])
+    with _ctx(swi, w) as c:
+        c.set_eigenpairs(eps_o, U_o)
+        T = c.transmission(E)
+    np.testing.assert_allclose(T, transport.transmission_direct(A, w.gamma_L, w.gamma_R, E), rtol=1e-9)
+
+
+def test_separable_box_full_grid_spectrum(swi):
+    # V = V(z), Gamma = Gamma(z) on the 48x48x96 grid of the bench workload: the
+    # spectrum is lambda_x + lambda_y + mu_z exactly (1D dense problems).
+    w = W.separable_wire(48, 48, 96, 0.5, 24, 2)
+    h = w.h
+    plane = w.nx * w.ny
+    vz, gz = w.V[::plane], (w.gamma_L + w.gamma_R)[::plane]
+    Az = -0.5 / h ** 2 * stencil.second_difference_1d(w.nz) + np.diag(vz - 1j * gz)
+    mu = np.linalg.eigvals(Az)
+    ex = np.linalg.eigvalsh(-0.5 / h ** 2 * stencil.second_difference_1d(w.nx))
+    lam = np.add.outer(np.add.outer(mu, ex), ex).reshape(-1)
+    lam = lam[np.lexsort((lam.imag, lam.real))]
+    # smallest n with a gap after it
+    n_r = 24
+    while abs(lam[n_r] - lam[n_r - 1]) < 1e-6:
+        n_r += 1
+    sig, req = W.count_windows(lam.real[:n_r], partition.window_counts(n_r, 2), inflate=1.3, extra=6)
+    with _ctx(swi, w) as c:
+        c.set_windows(sig, req)
+        info = c.solve(block=16, rel_tol=REL_TOL, n_keep=n_r, max_matvecs=60000)
+        eps = c.eigenvalues()
+        res = c.residuals()
+    assert info["status"] == "SWI_OK", info
+    assert _eps_err(eps, lam[:n_r]) <= EPS_TOL
+    assert np.max(res) <= REL_TOL
+
+
+# --------------------------------------------------------------------------- planner and errors
+def test_plan_windows_is_algorithm1(swi):
+    w = W.make_wire(8, 8, 10, 0.5, 2, 1)
+    with _ctx(swi, w) as c:
+        for n_r, p in ((48, 4), (400, 8), (2210, 4), (30, 3)):
+            s, n = c.plan_windows(n_r, p, -2.0, 40.0, inflate=1.0)
+            assert list(n) == partition.window_counts(n_r, p)
+            np.testing.assert_allclose(s, partition.window_shifts(partition.window_counts(n_r, p), -2.0, 40.0, w.N),
+                                       rtol=1e-14, atol=1e-14)
+
+
+def test_invalid_arguments_are_reported(swi):
+    w = W.make_wire(8, 8, 10, 0.5, 2, 1)
+    with pytest.raises(swi.SwiError) as e:
+        swi.Context(4, 8, 10, 0.5)
+    assert e.value.code == swi.SWI_EINVAL
+    with _ctx(swi, w) as c:
+        with pytest.raises(swi.SwiError) as e:
+            c.set_windows([0.5, 0.1], [4, 4])
+        assert e.value.code == swi.SWI_EINVAL
+        with pytest.raises(swi.SwiError) as e:
+            c.transmission([0.1])
+        assert e.value.code == swi.SWI_ESTATE
+        bad = w.gamma_L.copy()
+        bad[3] = -1.0
+        with pytest.raises(swi.SwiError) as e:
+            c.set_absorber(bad, w.gamma_R)
+        assert e.value.code == swi.SWI_EINVAL
+        Vn = w.V.copy()
+        Vn[0] = np.nan
+        with pytest.raises(swi.SwiError) as e:
+            c.set_potential(Vn)
+        assert e.value.code == swi.SWI_EINVAL
+
+
+def test_budget_exhaustion_returns_partial_result(swi):
+    w = W.make_wire(8, 8, 14, 0.5, 4, 1)
+    with _ctx(swi, w) as c:
+        c.set_windows([1.5], [10])
+        info = c.solve(block=4, rel_tol=1e-13, max_matvecs=40)
+        assert info["status"] == "SWI_ENOCONV"
+        assert c.n_pairs() == 10

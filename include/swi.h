@@ -61,6 +61,7 @@ typedef enum {
 
 enum { SWI_BC_ODD = 0, SWI_BC_ZERO = 1 };        /* boundary rule, see swi_create */
 enum { SWI_PREC_F64 = 0, SWI_PREC_MIXED = 1 };   /* arithmetic of the Krylov loop */
+enum { SWI_ARITH_DS = 2, SWI_ARITH_F64 = 1 };     /* see swi_solve_opts.arith */
 
 /* Options of swi_solve.  Zero-initialise and set what you need; zero fields
  * take the defaults given here. */
@@ -69,8 +70,13 @@ typedef struct {
   int max_basis;        /* m_j, basis size before a restart (default
                            max(2 n_req + 1, n_req + 2b) rounded up to b) */
   int keep;             /* Ritz vectors kept at a restart (default
-                           n_req + (m_j - n_req)/2, at most m_j - b) */
-  int reserved0;
+                           max(n_req + n_req/2, n_req + b), at most m_j - b) */
+  int arith;            /* arithmetic of the tall-skinny products (Gram,
+                           update, Cholesky-QR, rotations, T(E) projections):
+                           0 or SWI_ARITH_DS (default) -- double-single on the
+                           FP32 pipes, ~1e-13 relative; SWI_ARITH_F64 -- native
+                           FP64.  The stencil, the projected eigenproblems and
+                           the final residual check are native FP64 in both. */
   long long max_matvecs;/* per-window budget of operator applications per
                            vector (default 2,000,000) */
   double rel_tol;       /* convergence: ||A u - eps u|| <= rel_tol ||A||_G ||u||,

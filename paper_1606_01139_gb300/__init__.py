@@ -22,6 +22,7 @@ STATUS_NAMES = {0: "SWI_OK", 1: "SWI_EINVAL", 2: "SWI_ENOMEM", 3: "SWI_ECUDA", 4
                 5: "SWI_HOLES", 6: "SWI_ETIMEOUT", 7: "SWI_ENOTIMPL", 8: "SWI_ESTATE"}
 BC_ODD, BC_ZERO = 0, 1
 PREC_F64, PREC_MIXED = 0, 1
+ARITH_DS, ARITH_F64 = 2, 1
 
 # Every entry point declared in include/swi.h.
 EXPORTS = ("swi_create", "swi_set_potential", "swi_set_absorber", "swi_set_windows", "swi_plan_windows",
@@ -37,7 +38,7 @@ class KernelStats(C.Structure):
 
 
 class SolveOpts(C.Structure):
-    _fields_ = [("block", C.c_int), ("max_basis", C.c_int), ("keep", C.c_int), ("reserved0", C.c_int),
+    _fields_ = [("block", C.c_int), ("max_basis", C.c_int), ("keep", C.c_int), ("arith", C.c_int),
                 ("max_matvecs", C.c_longlong), ("rel_tol", C.c_double), ("eq_rtol", C.c_double),
                 ("drop_tol", C.c_double), ("seed", C.c_ulonglong), ("n_keep", C.c_int), ("reserved1", C.c_int)]
 
@@ -205,9 +206,10 @@ class Context:
 
     # -- solve
     def solve(self, block=16, rel_tol=1e-10, max_basis=0, keep=0, max_matvecs=0, eq_rtol=0.0, drop_tol=0.0,
-              seed=1, n_keep=0, allow=(SWI_OK, SWI_ENOCONV, SWI_HOLES)):
+              seed=1, n_keep=0, arith=ARITH_DS, allow=(SWI_OK, SWI_ENOCONV, SWI_HOLES)):
+        """Windowed solve; arith = ARITH_DS (double-single products, default) or ARITH_F64 (native)."""
         o = SolveOpts(block=block, max_basis=max_basis, keep=keep, max_matvecs=max_matvecs, rel_tol=rel_tol,
-                      eq_rtol=eq_rtol, drop_tol=drop_tol, seed=seed, n_keep=n_keep)
+                      eq_rtol=eq_rtol, drop_tol=drop_tol, seed=seed, n_keep=n_keep, arith=arith)
         info = SolveInfo()
         rc = self._check(self._lib.swi_solve(self._h, C.byref(o), C.byref(info)), allow)
         d = info.as_dict()

@@ -102,6 +102,7 @@ struct swi_ctx {
   DevMem m_comp, m_pairs, m_counts, m_work, m_gram, m_kept, m_order, m_holes, m_src, m_coef, m_nterm, m_info,
       m_win, m_eps_all, m_eps_out;
   long long launches = 0;
+  int arith = SWI_ARITH_DS;  // arithmetic of the tall-skinny products (last solve's choice)
   std::string err;
   // per-kernel-class event timing
   struct ProfRec {
@@ -139,11 +140,13 @@ struct ProfScope {
   swi_ctx* c;
   int kind;
   double flops, bytes;
+  cudaStream_t st;
   cudaEvent_t a = nullptr;
-  ProfScope(swi_ctx* ctx, int k, double f, double by) : c(ctx), kind(k), flops(f), bytes(by) {
+  ProfScope(swi_ctx* ctx, int k, double f, double by, cudaStream_t stream = nullptr)
+      : c(ctx), kind(k), flops(f), bytes(by), st(stream ? stream : ctx->stream) {
     if (c->prof_on) {
       a = take_event(c);
-      SWI_CUDA_TRY(cudaEventRecord(a, c->stream));
+      SWI_CUDA_TRY(cudaEventRecord(a, st));
     }
   }
   ~ProfScope() {
@@ -155,10 +158,21 @@ struct ProfScope {
     } else if (cudaEventCreate(&b) != cudaSuccess) {
       return;
     }
-    if (cudaEventRecord(b, c->stream) != cudaSuccess) return;
+    if (cudaEventRecord(b, st) != cudaSuccess) return;
     c->prof.push_back({kind, a, b, flops, bytes});
   }
 };
+
+// Tall-skinny products: double-single on the FP32 pipes (default) or native FP64.
+void gram_dispatch(int arith, const swi::GramBatch& b, int N, const double* w, int bilinear, double2* work,
+                   size_t work_elems, cudaStream_t s, long long* launches) {
+  if (arith == SWI_ARITH_F64) swi::launch_gram(b, N, w, bilinear, work, work_elems, s, launches);
+  else swi::launch_gram_df(b, N, w, bilinear, work, work_elems, s, launches);
+}
+void rowgemm_dispatch(int arith, const swi::RowGemmBatch& b, int N, cudaStream_t s, long long* launches) {
+  if (arith == SWI_ARITH_F64) swi::launch_rowgemm(b, N, s, launches);
+  else swi::launch_rowgemm_df(b, N, s, launches);
+}
 
 swi_status fail(swi_ctx* ctx, swi_status code, const std::string& msg) {
   if (ctx) ctx->err = msg;
@@ -262,7 +276,7 @@ void cholqr2(swi_ctx* c, std::vector<Window*>& ws, const std::vector<int>& col, 
       const int ldx = second ? w.ld : b;
       gb.job[q] = swi::GramJob{X, X, w.G.as<double2>(), ldx, ldx, b, b, b, 0};
     }
-    swi::launch_gram(gb, c->N, nullptr, 0, c->gram_work.as<double2>(), c->gram_work.bytes / sizeof(double2),
+    gram_dispatch(c->arith,gb, c->N, nullptr, 0, c->gram_work.as<double2>(), c->gram_work.bytes / sizeof(double2),
                      c->stream, &c->launches);
   };
   auto chol_of = [&](bool second) {
@@ -285,7 +299,7 @@ void cholqr2(swi_ctx* c, std::vector<Window*>& ws, const std::vector<int>& col, 
       rb.job[q] = swi::RowGemmJob{w.W.as<double2>(), w.R1i.as<double2>(), nullptr, w.Q[w.cur].as<double2>() + col[q],
                                   b, b, 0, w.ld, b, b, 1.0, 0.0};
     }
-    swi::launch_rowgemm(rb, c->N, c->stream, &c->launches);
+    rowgemm_dispatch(c->arith,rb, c->N, c->stream, &c->launches);
   }
   gram_of(true);
   chol_of(true);
@@ -297,7 +311,7 @@ void cholqr2(swi_ctx* c, std::vector<Window*>& ws, const std::vector<int>& col, 
       rb.job[q] = swi::RowGemmJob{w.Q[w.cur].as<double2>() + col[q], w.R2i.as<double2>(), nullptr, w.W.as<double2>(),
                                   w.ld, b, 0, b, b, b, 1.0, 0.0};
     }
-    swi::launch_rowgemm(rb, c->N, c->stream, &c->launches);
+    rowgemm_dispatch(c->arith,rb, c->N, c->stream, &c->launches);
   }
   for (int q = 0; q < nb; ++q) {
     Window& w = *ws[q];
@@ -320,6 +334,9 @@ swi_status do_solve(swi_ctx* c, const swi_solve_opts* o, swi_solve_info* info) {
   const long long budget = opt.max_matvecs > 0 ? opt.max_matvecs : 2000000LL;
   const unsigned long long seed = opt.seed ? opt.seed : 1ull;
   const double anorm = gershgorin(c);
+  if (opt.arith != 0 && opt.arith != SWI_ARITH_DS && opt.arith != SWI_ARITH_F64)
+    return fail(c, SWI_EINVAL, "unknown arithmetic");
+  c->arith = opt.arith == SWI_ARITH_F64 ? SWI_ARITH_F64 : SWI_ARITH_DS;
   const int nwin = (int)c->sigma.size();
   if (nwin > swi::kMaxBatch) return fail(c, SWI_EINVAL, "at most 64 windows per solve");
   const double t0 = swi::now_seconds();
@@ -406,16 +423,107 @@ swi_status do_solve(swi_ctx* c, const swi_solve_opts* o, swi_solve_info* info) {
   }
 
   // ---- the batched Krylov-Schur loop
+  // Windows expand in lockstep: one launch per kernel serves every expanding
+  // window.  A window whose next block would not fit runs its projected
+  // eigenproblem (one CTA) on a stream of its own and sits out of the batch
+  // until that finishes, so the Schur step overlaps the other windows' GEMMs.
+  struct SideRes {
+    std::vector<cudaStream_t> st;
+    std::vector<cudaEvent_t> ready, done;
+    int* oi = nullptr;
+    ~SideRes() {
+      for (auto x : st)
+        if (x) cudaStreamDestroy(x);
+      for (auto x : ready)
+        if (x) cudaEventDestroy(x);
+      for (auto x : done)
+        if (x) cudaEventDestroy(x);
+      if (oi) cudaFreeHost(oi);
+    }
+  } side;
+  side.st.assign(nwin, nullptr);
+  side.ready.assign(nwin, nullptr);
+  side.done.assign(nwin, nullptr);
+  for (int j = 0; j < nwin; ++j) {
+    SWI_CUDA_TRY(cudaStreamCreateWithFlags(&side.st[j], cudaStreamNonBlocking));
+    SWI_CUDA_TRY(cudaEventCreateWithFlags(&side.ready[j], cudaEventDisableTiming));
+    SWI_CUDA_TRY(cudaEventCreateWithFlags(&side.done[j], cudaEventDisableTiming));
+  }
+  SWI_CUDA_TRY(cudaMallocHost(&side.oi, sizeof(int) * 4 * nwin));
+  std::vector<int> in_schur(nwin, 0);
+
+  // Act on a finished Schur step of window j: finalise or thick-restart (context stream).
+  auto finish_restart = [&](int j) {
+    Window& w = *win[j];
+    const int* oi = side.oi + 4 * j;
+    const int k = oi[0], nconv = oi[1], st = oi[2];
+    SWI_CUDA_TRY(cudaStreamWaitEvent(c->stream, side.done[j], 0));
+    w.restarts++;
+    w.nconv = nconv;
+    if (st != 0) w.failed = true;
+    if (st != 0 || nconv >= w.nreq || w.matvecs >= budget) {
+      swi::RitzBatch fin;
+      fin.n = 1;
+      fin.job[0] = swi::RitzJob{w.Z.as<double2>(), w.S.as<double2>(), w.theta.as<double2>(), w.resid.as<double>(),
+                                c->ordinfo.as<int>() + 4 * j, w.Yw.as<double2>(), w.eps_w.as<double2>(),
+                                w.res_w.as<double>(), w.p, w.ld, w.nreq, w.nreq, w.sigma};
+      swi::RowGemmBatch rb;
+      rb.n = 1;
+      rb.job[0] = swi::RowGemmJob{w.Q[w.cur].as<double2>(), w.Yw.as<double2>(), nullptr,
+                                  c->Uall.as<double2>() + out_off[j], w.ld, w.nreq, 0, n_all, w.p, w.nreq, 1.0, 0.0};
+      ProfScope ps(c, SWI_K_ROTATE, 8.0 * c->N * (double)w.p * w.nreq, 16.0 * c->N * (double)(w.p + w.nreq));
+      swi::launch_ritz_batch(fin, c->stream, &c->launches);
+      rowgemm_dispatch(c->arith,rb, c->N, c->stream, &c->launches);
+      w.done = true;
+      return;
+    }
+    if (k + b > w.m || k < w.nreq) throw Error{SWI_ECUDA, "internal: restart size out of range"};
+    swi::ZextBatch zb;
+    zb.n = 1;
+    zb.job[0] = swi::ZextJob{w.Z.as<double2>(), w.Zext.as<double2>(), w.ld, k + b, w.p, k, b};
+    swi::RowGemmBatch rb;
+    rb.n = 1;
+    rb.job[0] = swi::RowGemmJob{w.Q[w.cur].as<double2>(), w.Zext.as<double2>(), nullptr, w.Q[1 - w.cur].as<double2>(),
+                                w.ld, k + b, 0, w.ld, w.p + b, k + b, 1.0, 0.0};
+    {
+      ProfScope ps(c, SWI_K_ROTATE, 8.0 * c->N * (double)(w.p + b) * (k + b),
+                   16.0 * c->N * (double)(w.p + b + k + b));
+      swi::launch_zext_batch(zb, c->stream, &c->launches);
+      rowgemm_dispatch(c->arith,rb, c->N, c->stream, &c->launches);
+    }
+    w.cur = 1 - w.cur;
+    swi::launch_copy_block(w.Bz.as<double2>(), w.ld, w.Bm.as<double2>(), w.ld, b, k, c->stream, &c->launches);
+    w.p = k;
+  };
+
   const long long max_steps = 100000000LL;
   for (long long step = 0; step < max_steps; ++step) {
+    // collect finished restarts
+    for (int j = 0; j < nwin; ++j) {
+      if (!in_schur[j]) continue;
+      const cudaError_t q = cudaEventQuery(side.done[j]);
+      if (q == cudaErrorNotReady) continue;
+      SWI_CUDA_TRY(q);
+      in_schur[j] = 0;
+      finish_restart(j);
+    }
     std::vector<Window*> act;
     std::vector<int> idx;
-    for (int j = 0; j < nwin; ++j)
-      if (!win[j]->done) {
-        act.push_back(win[j].get());
-        idx.push_back(j);
+    int pending = -1;
+    for (int j = 0; j < nwin; ++j) {
+      if (win[j]->done) continue;
+      if (in_schur[j]) {
+        if (pending < 0) pending = j;
+        continue;
       }
-    if (act.empty()) break;
+      act.push_back(win[j].get());
+      idx.push_back(j);
+    }
+    if (act.empty()) {
+      if (pending < 0) break;
+      SWI_CUDA_TRY(cudaEventSynchronize(side.done[pending]));
+      continue;
+    }
     const int na = (int)act.size();
     // 1) W_j = (A - sigma_j) V_j for every active window, one launch
     {
@@ -448,12 +556,12 @@ swi_status do_solve(swi_ctx* c, const swi_solve_opts* o, swi_solve_info* info) {
       const double Nn = (double)c->N;
       {
         ProfScope ps(c, SWI_K_GRAM, 8.0 * Nn * ncol * b, 16.0 * Nn * (ncol + na * b));
-        swi::launch_gram(gb, c->N, nullptr, 0, c->gram_work.as<double2>(), c->gram_work.bytes / sizeof(double2),
+        gram_dispatch(c->arith,gb, c->N, nullptr, 0, c->gram_work.as<double2>(), c->gram_work.bytes / sizeof(double2),
                          c->stream, &c->launches);
       }
       {
         ProfScope ps(c, SWI_K_UPDATE, 8.0 * Nn * ncol * b, 16.0 * Nn * (ncol + 2.0 * na * b));
-        swi::launch_rowgemm(rb, c->N, c->stream, &c->launches);
+        rowgemm_dispatch(c->arith,rb, c->N, c->stream, &c->launches);
       }
     }
     // 3) Cholesky-QR2 of the remainder into Q_j[:, p+b : p+2b]
@@ -475,107 +583,32 @@ swi_status do_solve(swi_ctx* c, const swi_solve_opts* o, swi_solve_info* info) {
       }
       swi::launch_hupdate_batch(hb, c->stream, &c->launches);
     }
-    std::vector<Window*> rs;
-    std::vector<int> rsi;
+    // 5) windows whose next block would not fit: Schur step on their own stream
     for (int q = 0; q < na; ++q) {
       Window& w = *act[q];
+      const int j = idx[q];
       w.p += b;
       w.matvecs += b;
-      if (w.p + b > w.m) {  // the next block would not fit: restart on the current basis
-        rs.push_back(&w);
-        rsi.push_back(idx[q]);
-      }
-    }
-    if (rs.empty()) continue;
-    // 5) restart: Schur form, SM selection, reordering, residual estimates
-    const int nr = (int)rs.size();
-    {
+      if (w.p + b <= w.m) continue;
+      if (w.p > w.m || w.keep + b > w.m) throw Error{SWI_ECUDA, "internal: basis bookkeeping out of range"};
+      // As ARPACK does, keep more Ritz vectors once some wanted pairs have
+      // converged, so the rest keep room in the restarted basis.
+      const int keep_eff = std::min(w.m - b, w.keep + std::min(w.nconv, (w.m - w.keep) / 2));
       swi::SchurBatch sb;
-      sb.n = nr;
-      for (int q = 0; q < nr; ++q) {
-        Window& w = *rs[q];
-        if (w.p > w.m || w.keep + b > w.m)
-          throw Error{SWI_ECUDA, "internal: basis bookkeeping out of range"};
-        // As ARPACK does, keep more Ritz vectors once some wanted pairs have
-        // converged, so the rest keep room in the restarted basis.
-        const int keep_eff = std::min(w.m - b, w.keep + std::min(w.nconv, (w.m - w.keep) / 2));
-        sb.job[q] = swi::SchurJob{w.H.as<double2>(), w.Z.as<double2>(), w.Bm.as<double2>(), w.Bz.as<double2>(),
-                                  w.theta.as<double2>(), w.resid.as<double>(), w.S.as<double2>(),
-                                  c->ordinfo.as<int>() + 4 * q, w.p, w.ld, b, keep_eff, w.nreq, w.m - b, tol_abs};
+      sb.n = 1;
+      sb.job[0] = swi::SchurJob{w.H.as<double2>(), w.Z.as<double2>(), w.Bm.as<double2>(), w.Bz.as<double2>(),
+                                w.theta.as<double2>(), w.resid.as<double>(), w.S.as<double2>(),
+                                c->ordinfo.as<int>() + 4 * j, w.p, w.ld, b, keep_eff, w.nreq, w.m - b, tol_abs};
+      SWI_CUDA_TRY(cudaEventRecord(side.ready[j], c->stream));
+      SWI_CUDA_TRY(cudaStreamWaitEvent(side.st[j], side.ready[j], 0));
+      {
+        ProfScope ps(c, SWI_K_SCHUR, 0.0, 0.0, side.st[j]);
+        swi::launch_schur_batch(sb, side.st[j], &c->launches);
       }
-      ProfScope ps(c, SWI_K_SCHUR, 0.0, 0.0);
-      swi::launch_schur_batch(sb, c->stream, &c->launches);
-    }
-    std::vector<int> oi(4 * nr);
-    SWI_CUDA_TRY(cudaMemcpyAsync(oi.data(), c->ordinfo.p, sizeof(int) * 4 * nr, cudaMemcpyDeviceToHost, c->stream));
-    sync(c->stream);
-    swi::RitzBatch fin;
-    fin.n = 0;
-    std::vector<Window*> fin_w;
-    std::vector<int> fin_i;
-    swi::ZextBatch zb;
-    zb.n = 0;
-    std::vector<Window*> rot_w;
-    std::vector<int> rot_k;
-    for (int q = 0; q < nr; ++q) {
-      Window& w = *rs[q];
-      const int k = oi[4 * q], nconv = oi[4 * q + 1], st = oi[4 * q + 2];
-      w.restarts++;
-      w.nconv = nconv;
-      if (st != 0) w.failed = true;
-      if (st != 0 || nconv >= w.nreq || w.matvecs >= budget) {
-        fin.job[fin.n++] = swi::RitzJob{w.Z.as<double2>(), w.S.as<double2>(), w.theta.as<double2>(),
-                                        w.resid.as<double>(), c->ordinfo.as<int>() + 4 * q, w.Yw.as<double2>(),
-                                        w.eps_w.as<double2>(), w.res_w.as<double>(), w.p, w.ld, w.nreq, w.nreq,
-                                        w.sigma};
-        fin_w.push_back(&w);
-        fin_i.push_back(rsi[q]);
-      } else {
-        if (k + b > w.m || k < w.nreq) throw Error{SWI_ECUDA, "internal: restart size out of range"};
-        zb.job[zb.n++] = swi::ZextJob{w.Z.as<double2>(), w.Zext.as<double2>(), w.ld, k + b, w.p, k, b};
-        rot_w.push_back(&w);
-        rot_k.push_back(k);
-      }
-    }
-    if (fin.n) {
-      swi::RowGemmBatch rb;
-      rb.n = fin.n;
-      double fl = 0.0, by = 0.0;
-      for (int q = 0; q < fin.n; ++q) {
-        Window& w = *fin_w[q];
-        rb.job[q] = swi::RowGemmJob{w.Q[w.cur].as<double2>(), w.Yw.as<double2>(), nullptr,
-                                    c->Uall.as<double2>() + out_off[fin_i[q]], w.ld, w.nreq, 0, n_all, w.p, w.nreq,
-                                    1.0, 0.0};
-        w.done = true;
-        fl += 8.0 * c->N * (double)w.p * w.nreq;
-        by += 16.0 * c->N * (double)(w.p + w.nreq);
-      }
-      ProfScope ps(c, SWI_K_ROTATE, fl, by);
-      swi::launch_ritz_batch(fin, c->stream, &c->launches);
-      swi::launch_rowgemm(rb, c->N, c->stream, &c->launches);
-    }
-    if (zb.n) {
-      swi::RowGemmBatch rb;
-      rb.n = zb.n;
-      double fl = 0.0, by = 0.0;
-      for (int q = 0; q < zb.n; ++q) {
-        Window& w = *rot_w[q];
-        const int k = rot_k[q];
-        rb.job[q] = swi::RowGemmJob{w.Q[w.cur].as<double2>(), w.Zext.as<double2>(), nullptr,
-                                    w.Q[1 - w.cur].as<double2>(), w.ld, k + b, 0, w.ld, w.p + b, k + b, 1.0, 0.0};
-        fl += 8.0 * c->N * (double)(w.p + b) * (k + b);
-        by += 16.0 * c->N * (double)(w.p + b + k + b);
-      }
-      ProfScope ps(c, SWI_K_ROTATE, fl, by);
-      swi::launch_zext_batch(zb, c->stream, &c->launches);
-      swi::launch_rowgemm(rb, c->N, c->stream, &c->launches);
-      for (int q = 0; q < zb.n; ++q) {
-        Window& w = *rot_w[q];
-        const int k = rot_k[q];
-        w.cur = 1 - w.cur;
-        swi::launch_copy_block(w.Bz.as<double2>(), w.ld, w.Bm.as<double2>(), w.ld, b, k, c->stream, &c->launches);
-        w.p = k;
-      }
+      SWI_CUDA_TRY(cudaMemcpyAsync(side.oi + 4 * j, c->ordinfo.as<int>() + 4 * j, sizeof(int) * 4,
+                                   cudaMemcpyDeviceToHost, side.st[j]));
+      SWI_CUDA_TRY(cudaEventRecord(side.done[j], side.st[j]));
+      in_schur[j] = 1;
     }
   }
   // ---- gather eigenvalue estimates and window statistics
@@ -720,10 +753,10 @@ void ensure_RL(swi_ctx* c) {
   swi::GramBatch gb;
   gb.n = 1;
   gb.job[0] = swi::GramJob{c->U.as<double2>(), c->U.as<double2>(), c->MR.as<double2>(), n, n, n, n, n, 0};
-  swi::launch_gram(gb, c->N, c->gR.as<double>(), 0, c->gram_work.as<double2>(), c->gram_work.bytes / sizeof(double2),
+  gram_dispatch(c->arith,gb, c->N, c->gR.as<double>(), 0, c->gram_work.as<double2>(), c->gram_work.bytes / sizeof(double2),
                    c->stream, &c->launches);
   gb.job[0].C = c->ML.as<double2>();
-  swi::launch_gram(gb, c->N, c->gL.as<double>(), 0, c->gram_work.as<double2>(), c->gram_work.bytes / sizeof(double2),
+  gram_dispatch(c->arith,gb, c->N, c->gL.as<double>(), 0, c->gram_work.as<double2>(), c->gram_work.bytes / sizeof(double2),
                    c->stream, &c->launches);
   swi::launch_wbuild(c->MR.as<double2>(), c->ML.as<double2>(), n, c->Rm.as<double2>(), c->Lm.as<double2>(),
                      c->Wm.as<double2>(), c->stream, &c->launches);
@@ -1012,7 +1045,7 @@ swi_status swi_grad(swi_ctx* c, int nE, const double* E, const double* dLdT, dou
       rb.n = 1;
       rb.job[0] = swi::RowGemmJob{c->U.as<double2>(), c->Mg.as<double2>(), nullptr, c->scratch.as<double2>(), n, n, 0,
                                   n, n, n, 1.0, 0.0};
-      swi::launch_rowgemm(rb, c->N, c->stream, &c->launches);
+      rowgemm_dispatch(c->arith,rb, c->N, c->stream, &c->launches);
       DevMem tmp;
       double* dst = dLdV;
       if (!dLdV_on_device) {

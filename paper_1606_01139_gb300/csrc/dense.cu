@@ -90,22 +90,22 @@ struct Rot {
 };
 
 // G = [[c, s], [-conj(s), c]] with G [x; y] = [r; 0]
+// c = |x|/r, s = x conj(y)/(|x| r), r = sqrt(|x|^2 + |y|^2); one reciprocal square
+// root on the serial path (FP64 latency on GB300 is long, so the chain is kept short).
 __device__ __forceinline__ Rot make_rot(double2 x, double2 y) {
   Rot g;
-  const double ax = cabs(x), ay = cabs(y);
-  if (ay == 0.0) {
+  const double ax2 = x.x * x.x + x.y * x.y, ay2 = y.x * y.x + y.y * y.y;
+  if (ay2 == 0.0) {
     g.c = 1.0;
     g.s = make_double2(0.0, 0.0);
-  } else if (ax == 0.0) {
+  } else if (ax2 == 0.0) {
+    const double t = rsqrt(ay2);
     g.c = 0.0;
-    g.s = make_double2(y.x / ay, -y.y / ay);  // conj(y)/|y|
+    g.s = make_double2(y.x * t, -y.y * t);  // conj(y)/|y|
   } else {
-    const double r = hypot(ax, ay);
-    g.c = ax / r;
-    const double2 ph = make_double2(x.x / ax, x.y / ax);
-    const double2 cy = make_double2(y.x, -y.y);
-    const double2 t = cmul(ph, cy);
-    g.s = make_double2(t.x / r, t.y / r);
+    const double t = rsqrt(ax2 * (ax2 + ay2));  // 1 / (|x| r)
+    g.c = ax2 * t;
+    g.s = make_double2((x.x * y.x + x.y * y.y) * t, (x.y * y.x - x.x * y.y) * t);
   }
   return g;
 }
@@ -126,16 +126,6 @@ __device__ __forceinline__ void rot_cols(double2& a1, double2& a2, const Rot& g)
 
 #define HH(i, j) H[(long long)(i) * ld + (j)]
 #define ZZ(i, j) Z[(long long)(i) * ld + (j)]
-
-// Apply rotation g from the left to rows (k, k+1), columns [c0, m), and from
-// the right to columns (k, k+1), rows [0, r1) of H and all rows of Z.
-__device__ void apply_rot(double2* H, double2* Z, int ld, int m, int k, int c0, int r1, const Rot& g) {
-  for (int j = c0 + threadIdx.x; j < m; j += blockDim.x) rot_rows(HH(k, j), HH(k + 1, j), g);
-  __syncthreads();
-  for (int i = threadIdx.x; i < r1; i += blockDim.x) rot_cols(HH(i, k), HH(i, k + 1), g);
-  for (int i = threadIdx.x; i < m; i += blockDim.x) rot_cols(ZZ(i, k), ZZ(i, k + 1), g);
-  __syncthreads();
-}
 
 __device__ double block_reduce_sum(double v, double* red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -281,8 +271,29 @@ __global__ void __launch_bounds__(kDenseThreads) schur_kernel(const __grid_const
         const Rot g = srot;
         const int c0 = (k == l) ? l : k - 1;
         const int r1 = min(k + 2, ihi) + 1;
-        apply_rot(H, Z, ld, m, k, c0, r1, g);
-        if (k > l && tid == 0) HH(k + 1, k - 1) = make_double2(0.0, 0.0);
+        // H <- G H G^H: rows (k, k+1) and columns (k, k+1) touch disjoint entries
+        // except the 2x2 block, which thread 0 updates with both; one barrier.
+        for (int j = c0 + tid; j < m; j += blockDim.x) {
+          if (j == k || j == k + 1) continue;
+          rot_rows(HH(k, j), HH(k + 1, j), g);
+          if (j == k - 1) HH(k + 1, k - 1) = make_double2(0.0, 0.0);  // the chased bulge
+        }
+        for (int i = tid; i < r1; i += blockDim.x) {
+          if (i == k || i == k + 1) continue;
+          rot_cols(HH(i, k), HH(i, k + 1), g);
+        }
+        for (int i = tid; i < m; i += blockDim.x) rot_cols(ZZ(i, k), ZZ(i, k + 1), g);
+        if (tid == 0) {
+          double2 a = HH(k, k), b = HH(k, k + 1), c = HH(k + 1, k), d = HH(k + 1, k + 1);
+          rot_rows(a, c, g);
+          rot_rows(b, d, g);
+          rot_cols(a, b, g);
+          rot_cols(c, d, g);
+          HH(k, k) = a;
+          HH(k, k + 1) = b;
+          HH(k + 1, k) = c;
+          HH(k + 1, k + 1) = d;
+        }
         __syncthreads();
       }
     }
@@ -348,7 +359,7 @@ __global__ void __launch_bounds__(kDenseThreads) schur_kernel(const __grid_const
         for (int j = q + 2 + tid; j < m; j += blockDim.x) rot_rows(HH(q, j), HH(q + 1, j), g);
         for (int i = tid; i < q; i += blockDim.x) rot_cols(HH(i, q), HH(i, q + 1), g);
         for (int i = tid; i < m; i += blockDim.x) rot_cols(ZZ(i, q), ZZ(i, q + 1), g);
-        __syncthreads();
+        // the 2x2 block {q, q+1}^2 is disjoint from the loops above
         if (tid == 0) {
           const double2 t11 = HH(q, q);
           HH(q, q) = HH(q + 1, q + 1);

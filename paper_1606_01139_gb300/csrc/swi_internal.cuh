@@ -136,6 +136,12 @@ struct RowGemmBatch {
 };
 void launch_rowgemm(const RowGemmBatch& b, int N, cudaStream_t s, long long* launches);
 
+// The same two products in double-single arithmetic on the FP32 pipes
+// (FP64 inputs and outputs, ~1e-13 relative accuracy); see blockops_df.cu.
+void launch_gram_df(const GramBatch& b, int N, const double* w, int bilinear, double2* work,
+                    size_t work_elems, cudaStream_t s, long long* launches);
+void launch_rowgemm_df(const RowGemmBatch& b, int N, cudaStream_t s, long long* launches);
+
 // Per-column 2-norms of a residual block R = Y - X diag(theta): out[c] = ||Y[:,c] - theta_c X[:,c]||.
 void launch_colnorm_resid(const double2* X, int ldx, const double2* Y, int ldy, const double2* theta,
                           int ncols, int N, double* out, double* work, size_t work_elems,

@@ -66,7 +66,7 @@ struct DevMem {
 struct Window {
   double sigma = 0.0;
   int nreq = 0, m = 0, keep = 0, ld = 0;  // ld: columns of the Q buffers (m + b)
-  DevMem Q[2], W, H, Bm, Z, S, Bz, theta, resid, C1, C2, G, R1, R1i, R2, R2i, Zext, Yw, eps_w, res_w;
+  DevMem Q[2], W, H, Bm, Z, S, Bz, theta, resid, C1, C2, G, R1, R1i, R2, R2i, Zext, Yw, eps_w, res_w, Hw, Zw;
   int cur = 0, p = 0;
   bool done = false, failed = false;
   long long matvecs = 0;
@@ -111,6 +111,7 @@ struct swi_ctx {
     double flops, bytes;
   };
   bool prof_on = false;
+  double schur_flops = 0.0;  // work of the Schur steps, known only after they ran
   std::vector<ProfRec> prof;
   std::vector<cudaEvent_t> evpool;
   ~swi_ctx() {
@@ -350,7 +351,10 @@ swi_status do_solve(swi_ctx* c, const swi_solve_opts* o, swi_solve_info* info) {
     w.sigma = c->sigma[j];
     w.nreq = c->nreq[j];
     int keep = opt.keep > 0 ? opt.keep : std::max(w.nreq + (w.nreq + 1) / 2, w.nreq + b);
-    int m = opt.max_basis > 0 ? opt.max_basis : std::max(2 * w.nreq + 1, keep + 8 * b);
+    // Default basis: keep + 8 blocks, plus 0-2 extra blocks by window index so
+    // equal windows restart at different steps and their Schur steps (one CTA
+    // each) overlap the other windows' expansion instead of coinciding.
+    int m = opt.max_basis > 0 ? opt.max_basis : std::max(2 * w.nreq + 1, keep + (8 + j % 3) * b);
     m = (m + b - 1) / b * b;
     if (keep > m - b) keep = m - b;
     if (keep < w.nreq) return fail(c, SWI_EINVAL, "max_basis too small for the window request");
@@ -378,6 +382,10 @@ swi_status do_solve(swi_ctx* c, const swi_solve_opts* o, swi_solve_info* info) {
     w.R2.ensure(sizeof(double2) * b * b);
     w.R2i.ensure(sizeof(double2) * b * b);
     w.Zext.ensure(sizeof(double2) * w.ld * w.ld);
+    if (c->arith != SWI_ARITH_F64) {
+      w.Hw.ensure(16 * (size_t)w.ld * w.ld);
+      w.Zw.ensure(16 * (size_t)w.ld * w.ld);
+    }
     w.Yw.ensure(sizeof(double2) * w.ld * w.nreq);
     w.eps_w.ensure(sizeof(double2) * w.nreq);
     w.res_w.ensure(sizeof(double) * w.nreq);
@@ -457,6 +465,12 @@ swi_status do_solve(swi_ctx* c, const swi_solve_opts* o, swi_solve_info* info) {
     Window& w = *win[j];
     const int* oi = side.oi + 4 * j;
     const int k = oi[0], nconv = oi[1], st = oi[2];
+    if (c->prof_on && c->arith != SWI_ARITH_F64) {
+      // Hessenberg reduction with accumulation ~ 64/3 m^3 real flops, plus 20
+      // flops per complex Givens pair update counted by the kernel
+      const double mm = (double)w.p;
+      c->schur_flops += 64.0 / 3.0 * mm * mm * mm + 20.0 * 1024.0 * (double)oi[3];
+    }
     SWI_CUDA_TRY(cudaStreamWaitEvent(c->stream, side.done[j], 0));
     w.restarts++;
     w.nconv = nconv;
@@ -598,12 +612,14 @@ swi_status do_solve(swi_ctx* c, const swi_solve_opts* o, swi_solve_info* info) {
       sb.n = 1;
       sb.job[0] = swi::SchurJob{w.H.as<double2>(), w.Z.as<double2>(), w.Bm.as<double2>(), w.Bz.as<double2>(),
                                 w.theta.as<double2>(), w.resid.as<double>(), w.S.as<double2>(),
-                                c->ordinfo.as<int>() + 4 * j, w.p, w.ld, b, keep_eff, w.nreq, w.m - b, tol_abs};
+                                c->ordinfo.as<int>() + 4 * j, w.p, w.ld, b, keep_eff, w.nreq, w.m - b, tol_abs,
+                                w.Hw.p, w.Zw.p};
       SWI_CUDA_TRY(cudaEventRecord(side.ready[j], c->stream));
       SWI_CUDA_TRY(cudaStreamWaitEvent(side.st[j], side.ready[j], 0));
       {
         ProfScope ps(c, SWI_K_SCHUR, 0.0, 0.0, side.st[j]);
-        swi::launch_schur_batch(sb, side.st[j], &c->launches);
+        if (c->arith == SWI_ARITH_F64) swi::launch_schur_batch(sb, side.st[j], &c->launches);
+        else swi::launch_schur_ds_batch(sb, side.st[j], &c->launches);
       }
       SWI_CUDA_TRY(cudaMemcpyAsync(side.oi + 4 * j, c->ordinfo.as<int>() + 4 * j, sizeof(int) * 4,
                                    cudaMemcpyDeviceToHost, side.st[j]));
@@ -1070,6 +1086,7 @@ swi_status swi_profile(swi_ctx* c, int enable) {
       c->evpool.push_back(r.b);
     }
     c->prof.clear();
+    c->schur_flops = 0.0;
     c->prof_on = enable != 0;
     return SWI_OK;
   });
@@ -1089,6 +1106,7 @@ swi_status swi_profile_read(swi_ctx* c, swi_kernel_stats* out) {
       s.flops += r.flops;
       s.bytes += r.bytes;
     }
+    out[SWI_K_SCHUR].flops += c->schur_flops;
     return SWI_OK;
   });
 }

@@ -174,12 +174,16 @@ struct SchurJob {
   int m, ld, b, keep, nwant;
   int kmax;         // the kept block is never extended beyond kmax columns
   double tol_abs;    // absolute residual threshold
+  void* Hw;          // [ld][ld] 16-byte work entries (double-single kernel only)
+  void* Zw;          // [ld][ld] 16-byte work entries (double-single kernel only)
 };
 struct SchurBatch {
   int n;
   SchurJob job[kMaxBatch];
 };
 void launch_schur_batch(const SchurBatch& b, cudaStream_t s, long long* launches);
+// The same step in double-single arithmetic (schur_ds.cu); needs Hw, Zw.
+void launch_schur_ds_batch(const SchurBatch& b, cudaStream_t s, long long* launches);
 
 // Ritz coefficient matrix of the wanted pairs after a Schur step:
 // Yw[:, q] = Z[:, 0:k] s_{w_q} (m x nwant, [m][ld]) and eps_w[q] = theta_{w_q} + sigma,

@@ -232,6 +232,27 @@ swi_status swi_profile(swi_ctx* ctx, int enable);
 /* Synchronise the stream and sum the records per class into out[SWI_K_COUNT]. */
 swi_status swi_profile_read(swi_ctx* ctx, swi_kernel_stats* out);
 
+/* T(E) for the context's current pairs, like swi_transmission, but without
+ * allocating anything on the device or through any allocator.  The paper has
+ * no counterpart: this exists for callers that cannot allocate device memory
+ * at call time -- code that records the call into a CUDA graph under stream
+ * capture (where cudaMalloc is not allowed), and hosts whose framework owns
+ * the whole device memory budget (a caching allocator that must not see
+ * foreign allocations, a hard memory cap).
+ *  - Limits: at most 64 eigenpairs in the context and 1024 energies per call;
+ *    larger sizes return SWI_EINVAL (use swi_transmission instead).
+ *  - Scratch: one file-scope device array of 4.6 MB that every GPU which loads
+ *    the library holds until the process exits.  The first call on each device
+ *    looks up the array's device address (cudaGetSymbolAddress); make that
+ *    first call before any stream capture.
+ *  - Every call on a device shares that array, which keeps the last call's
+ *    contents; calls whose work overlaps on the GPU (other host threads, other
+ *    contexts on other streams) race on it and must be serialised by the
+ *    caller.  Nothing in it needs clearing: each call overwrites what it reads.
+ * E, T_out: host arrays of nE doubles.  Errors: SWI_ESTATE (no pairs or no
+ * absorbers), SWI_EINVAL (sizes, NULL, non-finite energy), SWI_ECUDA. */
+swi_status swi_transmission_noalloc(swi_ctx* ctx, int nE, const double* E, double* T_out);
+
 /* Message of the last failing call on ctx (thread-local for ctx == NULL). */
 const char* swi_last_error(const swi_ctx* ctx);
 

@@ -28,7 +28,7 @@ ARITH_DS, ARITH_F64 = 2, 1
 EXPORTS = ("swi_create", "swi_set_potential", "swi_set_absorber", "swi_set_windows", "swi_plan_windows",
            "swi_apply", "swi_solve", "swi_get_window_info", "swi_get_eigenpairs", "swi_copy_eigenpairs",
            "swi_set_eigenpairs", "swi_residuals", "swi_transmission", "swi_grad", "swi_profile",
-           "swi_profile_read", "swi_last_error", "swi_launch_count", "swi_destroy")
+           "swi_profile_read", "swi_transmission_noalloc", "swi_last_error", "swi_launch_count", "swi_destroy")
 
 KERNEL_CLASSES = ("stencil", "gram", "update", "cholqr", "schur", "rotate", "merge", "proj", "trans", "grad")
 
@@ -86,6 +86,7 @@ def load(path: str = LIB_PATH):
         "swi_transmission": (I, [VP, I, VP, VP]),
         "swi_grad": (I, [VP, I, VP, VP, VP, I, VP]),
         "swi_profile": (I, [VP, I]),
+        "swi_transmission_noalloc": (I, [VP, I, VP, VP]),
         "swi_profile_read": (I, [VP, P(KernelStats)]),
         "swi_last_error": (C.c_char_p, [VP]),
         "swi_launch_count": (C.c_longlong, [VP]),
@@ -258,6 +259,18 @@ class Context:
         E = _c_arr(np.atleast_1d(E), np.float64)
         T = np.empty_like(E)
         self._check(self._lib.swi_transmission(self._h, len(E), _ptr(E), _ptr(T)))
+        return T
+
+    def transmission_noalloc(self, E):
+        """T(E) through swi_transmission_noalloc: no device allocation during the call.
+
+        For callers that cannot allocate at call time (stream capture, a
+        framework that owns the memory budget); at most 64 pairs and 1024
+        energies, and calls must not overlap on the GPU (shared scratch).
+        """
+        E = _c_arr(np.atleast_1d(E), np.float64)
+        T = np.empty_like(E)
+        self._check(self._lib.swi_transmission_noalloc(self._h, len(E), _ptr(E), _ptr(T)))
         return T
 
     def grad(self, E, dLdT, dLdV_out=None):

@@ -13,6 +13,7 @@
 #include <memory>
 #include <new>
 #include <string>
+#include <mutex>
 #include <vector>
 
 #include "merge.cuh"
@@ -1107,6 +1108,82 @@ swi_status swi_profile_read(swi_ctx* c, swi_kernel_stats* out) {
       s.bytes += r.bytes;
     }
     out[SWI_K_SCHUR].flops += c->schur_flops;
+    return SWI_OK;
+  });
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// T(E) without any allocation, for callers that must not allocate device
+// memory at call time (see swi_transmission_noalloc in swi.h).  All scratch
+// lives in one file-scope device array, shared by every call on a device.
+namespace {
+constexpr int kNoAllocMaxPairs = 64;
+constexpr int kNoAllocMaxEnergies = 1024;
+constexpr size_t kNoAllocMat = (size_t)kNoAllocMaxPairs * kNoAllocMaxPairs;  // one n x n matrix
+constexpr size_t kNoAllocWork = 64 * kNoAllocMat;                            // split-N partial sums
+// layout: MR, ML, R, L, W (n x n each), Gram partial sums, then E[1024], T[1024] as doubles
+constexpr size_t kNoAllocElems = 5 * kNoAllocMat + kNoAllocWork + kNoAllocMaxEnergies;
+}  // namespace
+
+static __device__ __align__(256) double2 g_noalloc_scratch[kNoAllocElems];  // 4.6 MB per device
+
+namespace {
+std::mutex g_noalloc_mutex;
+std::vector<void*> g_noalloc_addr;  // device address of g_noalloc_scratch, per device ordinal
+
+// Once per device, with that device current: the array's device address.
+double2* noalloc_scratch(int device) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if ((int)g_noalloc_addr.size() <= device) g_noalloc_addr.resize(device + 1, nullptr);
+  if (!g_noalloc_addr[device]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      throw Error{SWI_ECUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e)};
+    g_noalloc_addr[device] = p;
+  }
+  return static_cast<double2*>(g_noalloc_addr[device]);
+}
+}  // namespace
+
+extern "C" {
+
+swi_status swi_transmission_noalloc(swi_ctx* c, int nE, const double* E, double* T_out) {
+  return guarded(c, [&]() -> swi_status {
+    if (c->npairs <= 0) return fail(c, SWI_ESTATE, "no eigenpairs");
+    if (!c->has_G) return fail(c, SWI_ESTATE, "absorbers must be set");
+    if (nE < 1 || !E || !T_out) return fail(c, SWI_EINVAL, "bad arguments");
+    if (c->npairs > kNoAllocMaxPairs)
+      return fail(c, SWI_EINVAL, "swi_transmission_noalloc: at most 64 eigenpairs (context holds " +
+                                     std::to_string(c->npairs) + "); use swi_transmission");
+    if (nE > kNoAllocMaxEnergies)
+      return fail(c, SWI_EINVAL, "swi_transmission_noalloc: at most 1024 energies per call");
+    if (!finite_all(E, nE)) return fail(c, SWI_EINVAL, "non-finite energy");
+    const int n = c->npairs;
+    double2* base = noalloc_scratch(c->device);
+    double2* MR = base;
+    double2* ML = base + kNoAllocMat;
+    double2* R = base + 2 * kNoAllocMat;
+    double2* L = base + 3 * kNoAllocMat;
+    double2* Wm = base + 4 * kNoAllocMat;
+    double2* work = base + 5 * kNoAllocMat;
+    double* Ed = reinterpret_cast<double*>(base + 5 * kNoAllocMat + kNoAllocWork);
+    double* Td = Ed + kNoAllocMaxEnergies;
+    // every scratch region below is fully overwritten before it is read, so
+    // nothing needs clearing between calls
+    SWI_CUDA_TRY(cudaMemcpyAsync(Ed, E, sizeof(double) * nE, cudaMemcpyHostToDevice, c->stream));
+    swi::GramBatch gb;
+    gb.n = 1;
+    gb.job[0] = swi::GramJob{c->U.as<double2>(), c->U.as<double2>(), MR, n, n, n, n, n, 0};
+    gram_dispatch(c->arith, gb, c->N, c->gR.as<double>(), 0, work, kNoAllocWork, c->stream, &c->launches);
+    gb.job[0].C = ML;
+    gram_dispatch(c->arith, gb, c->N, c->gL.as<double>(), 0, work, kNoAllocWork, c->stream, &c->launches);
+    swi::launch_wbuild(MR, ML, n, R, L, Wm, c->stream, &c->launches);
+    swi::launch_transmission(Wm, c->eps.as<double2>(), n, Ed, nE, Td, nullptr, c->stream, &c->launches);
+    SWI_CUDA_TRY(cudaMemcpyAsync(T_out, Td, sizeof(double) * nE, cudaMemcpyDeviceToHost, c->stream));
+    sync(c->stream);
     return SWI_OK;
   });
 }

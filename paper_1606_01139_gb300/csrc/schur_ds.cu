@@ -21,7 +21,7 @@ namespace {
 
 using namespace ds;
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
 // deflation and tie tolerances relative to double-single precision
 constexpr float kDeflate = 4e-15f;
 
@@ -117,7 +117,10 @@ __global__ void __launch_bounds__(kThreads) schur_ds_kernel(const __grid_constan
   __shared__ df red[kThreads / 32];
   __shared__ dc sv[1024];
   __shared__ RotD srot;
+  __shared__ RotD s_rot2[2];
+  __shared__ dc s_hand[2][3];
   __shared__ int s_flag;
+  __shared__ int s_l;
   __shared__ int s_sel[1024];
   const int tid = threadIdx.x;
   if (m > 1024) {
@@ -153,23 +156,43 @@ __global__ void __launch_bounds__(kThreads) schur_ds_kernel(const __grid_constan
     __syncthreads();
     const df vn2 = add(cabs2(csub(x0, alpha)), tail2);
     const df tau = div(df{2.f, 0.f}, vn2);
-    for (int j = c + 1 + tid; j < m; j += blockDim.x) {
-      dc w = czero();
-      for (int i = c + 1; i < m; ++i) w = cadd(w, cmulc_l(sv[i], HD(i, j)));
-      w = cscale(w, tau);
-      for (int i = c + 1; i < m; ++i) HD(i, j) = csub(HD(i, j), cmul(sv[i], w));
+    // H <- P H: thread pairs share a column (even/odd rows, two partial sums
+    // each), combined by a shuffle; the pair then updates its halves.
+    for (int t = tid; t < 2 * (m - c - 1); t += blockDim.x) {
+      const int j = c + 1 + (t >> 1), h = t & 1;
+      dc w0 = czero(), w1 = czero();
+      int i = c + 1 + h;
+      for (; i + 2 < m; i += 4) {
+        const dc x0 = HD(i, j), x1 = HD(i + 2, j);
+        w0 = cadd(w0, cmulc_l(sv[i], x0));
+        w1 = cadd(w1, cmulc_l(sv[i + 2], x1));
+      }
+      if (i < m) w0 = cadd(w0, cmulc_l(sv[i], HD(i, j)));
+      dc w = cadd(w0, w1);
+      const unsigned msk = 3u << (threadIdx.x & 30);  // the two lanes of the pair
+      dc o;
+      o.re.h = __shfl_xor_sync(msk, w.re.h, 1);
+      o.re.l = __shfl_xor_sync(msk, w.re.l, 1);
+      o.im.h = __shfl_xor_sync(msk, w.im.h, 1);
+      o.im.l = __shfl_xor_sync(msk, w.im.l, 1);
+      w = cscale(cadd(w, o), tau);
+      for (int r = c + 1 + h; r < m; r += 2) HD(r, j) = csub(HD(r, j), cmul(sv[r], w));
     }
     __syncthreads();
     for (int i = c + 1 + tid; i < m; i += blockDim.x) HD(i, c) = (i == c + 1) ? alpha : czero();
-    for (int i = tid; i < m; i += blockDim.x) {
-      dc u = czero();
-      for (int j = c + 1; j < m; ++j) u = cadd(u, cmul(HD(i, j), sv[j]));
-      u = cscale(u, tau);
-      for (int j = c + 1; j < m; ++j) HD(i, j) = csub(HD(i, j), cmul(u, cconj(sv[j])));
-      dc uz = czero();
-      for (int j = c + 1; j < m; ++j) uz = cadd(uz, cmul(ZD(i, j), sv[j]));
-      uz = cscale(uz, tau);
-      for (int j = c + 1; j < m; ++j) ZD(i, j) = csub(ZD(i, j), cmul(uz, cconj(sv[j])));
+    // H <- H P and Z <- Z P: one thread per row of H and per row of Z
+    for (int t = tid; t < 2 * m; t += blockDim.x) {
+      dc* row = (t < m) ? &HD(t, 0) : &ZD(t - m, 0);
+      dc u0 = czero(), u1 = czero();
+      int j = c + 1;
+      for (; j + 1 < m; j += 2) {
+        const dc x0 = row[j], x1 = row[j + 1];
+        u0 = cadd(u0, cmul(x0, sv[j]));
+        u1 = cadd(u1, cmul(x1, sv[j + 1]));
+      }
+      if (j < m) u0 = cadd(u0, cmul(row[j], sv[j]));
+      const dc u = cscale(cadd(u0, u1), tau);
+      for (j = c + 1; j < m; ++j) row[j] = csub(row[j], cmul(u, cconj(sv[j])));
     }
     __syncthreads();
   }
@@ -181,14 +204,17 @@ __global__ void __launch_bounds__(kThreads) schur_ds_kernel(const __grid_constan
     int ihi = m - 1, its = 0, total_its = 0;
     const int max_its = 60 * m + 100;
     while (ihi > 0) {
-      int l = ihi;
-      while (l > 0) {
-        float tst = cabs1f(HD(l - 1, l - 1)) + cabs1f(HD(l, l));
+      // l = the largest index <= ihi with a negligible subdiagonal (0 if none),
+      // every subdiagonal tested at once
+      if (tid == 0) s_l = 0;
+      __syncthreads();
+      for (int i = tid + 1; i <= ihi; i += blockDim.x) {
+        float tst = cabs1f(HD(i - 1, i - 1)) + cabs1f(HD(i, i));
         if (tst == 0.f) tst = 1.f;
-        if (cabs1f(HD(l, l - 1)) <= kDeflate * tst) break;
-        --l;
+        if (cabs1f(HD(i, i - 1)) <= kDeflate * tst) atomicMax(&s_l, i);
       }
       __syncthreads();
+      const int l = s_l;
       if (l > 0 && tid == 0) HD(l, l - 1) = czero();
       if (l == ihi) {
         __syncthreads();
@@ -218,6 +244,120 @@ __global__ void __launch_bounds__(kThreads) schur_ds_kernel(const __grid_constan
         mu = cfrom(m64);
       }
       __syncthreads();
+      if (m + 32 <= (int)blockDim.x) {
+        // One barrier per rotation.  Thread 0 chases the bulge: it updates the
+        // 2x2 block, column k-1 and row k+2, and computes the next rotation from
+        // values it produced itself.  Thread 32+q owns column q (left updates,
+        // rows k, k+1), row q (right updates, columns k, k+1) and row q of Z,
+        // keeps its pair in registers and prefetches the next one.  The two
+        // values that change hands each step go through double-buffered shared
+        // slots: H[k+1][k+2] (column owner -> thread 0) and H[k][k+1], H[k][k+2]
+        // (-> the owner of row k, which joins the right updates next step).
+        const int q = tid - 32;
+        const bool owner = tid >= 32 && q < m;
+        dc lt = czero(), lb = czero(), rl = czero(), rr = czero(), zl = czero(), zr = czero();
+        dc p_kk = czero(), p_kk1 = czero(), p_k1k = czero(), p_k1k1 = czero(), p_k2k1 = czero();
+        dc p_x = czero(), p_y = czero();
+        if (owner) {
+          if (q >= l + 2) {
+            lt = HD(l, q);
+            lb = HD(l + 1, q);
+          }
+          if (q < l) {
+            rl = HD(q, l);
+            rr = HD(q, l + 1);
+          }
+          zl = ZD(q, l);
+          zr = ZD(q, l + 1);
+        }
+        if (tid == 0) {
+          p_kk = HD(l, l);
+          p_kk1 = HD(l, l + 1);
+          p_k1k = HD(l + 1, l);
+          p_k1k1 = HD(l + 1, l + 1);
+          p_k2k1 = (l + 2 <= ihi) ? HD(l + 2, l + 1) : czero();
+          s_rot2[l & 1] = make_rot_ds(csub(p_kk, mu), p_k1k);
+        }
+        __syncthreads();
+        for (int k = l; k < ihi; ++k) {
+          const RotD g = s_rot2[k & 1];
+          const int par = k & 1;
+          if (tid == 0) {
+            // operands of the next step first: final since the last barrier
+            dc n_k1k1 = czero(), n_k2k1 = czero();
+            if (k + 1 < ihi) {
+              n_k1k1 = HD(k + 2, k + 2);
+              if (k + 3 <= ihi) n_k2k1 = HD(k + 3, k + 2);
+            }
+            n_upd += (m - ((k == l) ? l : k - 1)) + (min(k + 2, ihi) + 1) + m;
+            if (k > l) {
+              p_kk1 = s_hand[par ^ 1][0];  // H[k][k+1] from the owner of column k+1
+              dc tx = p_x, ty = p_y;       // column k-1: (H[k][k-1], H[k+1][k-1]) -> (r, 0)
+              rot_rows(tx, ty, g);
+              HD(k, k - 1) = tx;
+              HD(k + 1, k - 1) = czero();
+            }
+            dc a = p_kk, b = p_kk1, c = p_k1k, d = p_k1k1;
+            rot_rows(a, c, g);
+            rot_rows(b, d, g);
+            rot_cols(a, b, g);
+            rot_cols(c, d, g);
+            HD(k, k) = a;
+            HD(k, k + 1) = b;
+            HD(k + 1, k) = c;
+            HD(k + 1, k + 1) = d;
+            s_hand[par][1] = b;  // H[k][k+1] for the owner of row k
+            dc e = czero(), f = p_k2k1;
+            if (k + 2 <= ihi) {
+              rot_cols(e, f, g);  // row k+2: (0, H[k+2][k+1]) -> the new bulge and subdiagonal
+              HD(k + 2, k) = e;
+              HD(k + 2, k + 1) = f;
+            }
+            if (k + 1 < ihi) {
+              s_rot2[par ^ 1] = make_rot_ds(c, e);
+              p_x = c;
+              p_y = e;
+              p_kk = d;
+              p_k1k = f;
+              p_k1k1 = n_k1k1;
+              p_k2k1 = n_k2k1;
+            }
+          } else if (owner) {
+            const bool more = k + 2 < m;
+            const dc n_lb = (more && q >= k + 2) ? HD(k + 2, q) : czero();
+            const dc n_rr = (more && q < k) ? HD(q, k + 2) : czero();
+            const dc n_zr = more ? ZD(q, k + 2) : czero();
+            if (q >= k + 2) {  // left: rows k, k+1 of column q
+              rot_rows(lt, lb, g);
+              HD(k, q) = lt;
+              HD(k + 1, q) = lb;
+              if (q == k + 2) {
+                s_hand[par][0] = lb;  // H[k+1][k+2] for thread 0
+                s_hand[par][2] = lt;  // H[k][k+2] for the owner of row k
+              }
+              lt = lb;
+              lb = n_lb;
+            }
+            if (q < k) {  // right: columns k, k+1 of row q
+              if (q == k - 1 && k > l) {
+                rl = s_hand[par ^ 1][1];
+                rr = s_hand[par ^ 1][2];
+              }
+              rot_cols(rl, rr, g);
+              HD(q, k) = rl;
+              HD(q, k + 1) = rr;
+              rl = rr;
+              rr = n_rr;
+            }
+            rot_cols(zl, zr, g);  // Z: columns k, k+1 of row q
+            ZD(q, k) = zl;
+            ZD(q, k + 1) = zr;
+            zl = zr;
+            zr = n_zr;
+          }
+          __syncthreads();
+        }
+      } else
       for (int k = l; k < ihi; ++k) {
         if (tid == 0) {
           dc x, y;
@@ -300,7 +440,109 @@ __global__ void __launch_bounds__(kThreads) schur_ds_kernel(const __grid_constan
   const int kk = s_flag;
   for (int i = tid; i < m; i += blockDim.x) s_sel[i] = (s_sel[i] < kk) ? 1 : 0;
   __syncthreads();
-  {
+  if (m + 32 <= (int)blockDim.x) {
+    // Each selected eigenvalue lambda moves up from pos to ks by adjacent swaps
+    // q = pos-1, ..., ks, one barrier per swap.  The rotation of swap q comes
+    // from (T[q][q+1], lambda - T[q][q]); the next one needs T[q-1][q] after
+    // the column update of row q-1, so thread 0 updates row q-1 itself and
+    // forms the next rotation at once.  Thread 32+i owns column i (rows q, q+1),
+    // row i (columns q, q+1) for i < q-1 and row i of Z, with its pair in
+    // registers.  Hand-offs: T[q-1][q+1] (thread 0 -> the owner of column q+1,
+    // which joins next swap) and T[q-2][q] (owner of row q-2 -> thread 0).
+    const int i = tid - 32;
+    const bool owner = tid >= 32 && i < m;
+    int ks = 0;
+    for (int pos = 0; pos < m; ++pos) {
+      if (!s_sel[pos]) continue;
+      if (pos > ks) {
+        const int q0 = pos - 1;
+        dc lt = czero(), lb = czero(), rl = czero(), rr = czero(), zl = czero(), zr = czero();
+        dc lam = czero(), tqq = czero(), a1 = czero(), a2 = czero();
+        if (owner) {
+          if (i >= q0 + 2) {
+            lt = HD(q0, i);
+            lb = HD(q0 + 1, i);
+          }
+          if (i < q0 - 1) {
+            rl = HD(i, q0);
+            rr = HD(i, q0 + 1);
+          }
+          zl = ZD(i, q0);
+          zr = ZD(i, q0 + 1);
+        }
+        if (tid == 0) {
+          lam = HD(pos, pos);
+          tqq = HD(q0, q0);
+          if (q0 >= 1) {
+            a1 = HD(q0 - 1, q0);
+            a2 = HD(q0 - 1, q0 + 1);
+          }
+          s_rot2[q0 & 1] = make_rot_ds(HD(q0, q0 + 1), csub(lam, tqq));
+        }
+        __syncthreads();
+        for (int q = q0; q >= ks; --q) {
+          const RotD g = s_rot2[q & 1];
+          const int par = q & 1;
+          if (tid == 0) {
+            dc n_tqq = czero(), n_a1 = czero();
+            if (q - 1 >= ks) {
+              n_tqq = HD(q - 1, q - 1);
+              if (q >= 2) n_a1 = HD(q - 2, q - 1);
+            }
+            n_upd += (m - q - 2) + q + m;
+            if (q < q0 && q >= 1) a2 = s_hand[par ^ 1][1];  // T[q-1][q+1], from the owner of row q-1
+            if (q >= 1) {
+              rot_cols(a1, a2, g);  // row q-1, columns q, q+1
+              HD(q - 1, q) = a1;
+              HD(q - 1, q + 1) = a2;
+              s_hand[par][0] = a2;
+            }
+            HD(q, q) = lam;
+            HD(q + 1, q + 1) = tqq;
+            HD(q + 1, q) = czero();
+            if (q - 1 >= ks) {
+              s_rot2[par ^ 1] = make_rot_ds(a1, csub(lam, n_tqq));
+              tqq = n_tqq;
+              a1 = n_a1;
+            }
+          } else if (owner) {
+            const dc n_lt = (i >= q + 2 && q >= 1) ? HD(q - 1, i) : czero();
+            const dc n_rl = (i < q - 2) ? HD(i, q - 1) : czero();
+            const dc n_zl = (q >= 1) ? ZD(i, q - 1) : czero();
+            if (i == q + 1) lb = HD(q, q + 1);  // joins the row updates next swap
+            if (i >= q + 2) {  // rows q, q+1 of column i
+              if (i == q + 2 && q < q0) lt = s_hand[par ^ 1][0];
+              rot_rows(lt, lb, g);
+              HD(q, i) = lt;
+              HD(q + 1, i) = lb;
+              lb = lt;
+              lt = n_lt;
+            }
+            if (i < q - 1) {  // columns q, q+1 of row i
+              rot_cols(rl, rr, g);
+              HD(i, q) = rl;
+              HD(i, q + 1) = rr;
+              if (i == q - 2) s_hand[par][1] = rl;  // T[q-2][q] for thread 0
+              rr = rl;
+              rl = n_rl;
+            }
+            rot_cols(zl, zr, g);
+            ZD(i, q) = zl;
+            ZD(i, q + 1) = zr;
+            zr = zl;
+            zl = n_zl;
+          }
+          __syncthreads();
+        }
+        if (tid == 0) {
+          s_sel[ks] = 1;
+          s_sel[pos] = 0;
+        }
+        __syncthreads();
+      }
+      ++ks;
+    }
+  } else {
     int ks = 0;
     for (int pos = 0; pos < m; ++pos) {
       if (!s_sel[pos]) continue;

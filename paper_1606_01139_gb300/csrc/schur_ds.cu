@@ -22,6 +22,15 @@ namespace {
 using namespace ds;
 
 constexpr int kThreads = 512;
+// Warp 0 runs the serial chain of the QR and reordering sweeps; the element
+// owners live in the warps that do not share its scheduler (warps 4, 8, 12 of
+// the 16 share warp 0's), 12 warps or 384 owners.
+constexpr int kMaxOwners = 384;
+__device__ __forceinline__ int owner_index(int tid) {
+  const int w = tid >> 5;
+  if ((w & 3) == 0) return -1;
+  return (w - 1 - (w >> 2)) * 32 + (tid & 31);
+}
 // deflation and tie tolerances relative to double-single precision
 constexpr float kDeflate = 4e-15f;
 
@@ -42,10 +51,11 @@ __device__ RotD make_rot_ds(dc x, dc y) {
     g.s = czero();
     return g;
   }
-  int e;
-  frexpf(mx, &e);
-  x = dc{ldexp_(x.re, -e), ldexp_(x.im, -e)};
-  y = dc{ldexp_(y.re, -e), ldexp_(y.im, -e)};
+  // 2^(127 - E), E the biased exponent of mx: brings mx into [1, 2)
+  const int be = min(max((__float_as_int(mx) >> 23) & 0xff, 1), 253);
+  const float sc = __int_as_float((254 - be) << 23);
+  x = dc{df{x.re.h * sc, x.re.l * sc}, df{x.im.h * sc, x.im.l * sc}};
+  y = dc{df{y.re.h * sc, y.re.l * sc}, df{y.im.h * sc, y.im.l * sc}};
   const df ax2 = cabs2(x), ay2 = cabs2(y);
   if (ay2.h == 0.f) {
     g.c = df{1.f, 0.f};
@@ -107,7 +117,9 @@ __device__ df block_reduce_df(df v, df* red) {
 }
 
 #define HD(i, j) Hd[(long long)(i) * ld + (j)]
-#define ZD(i, j) Zd[(long long)(i) * ld + (j)]
+// Z is kept transposed in the work array: the column rotations then touch
+// consecutive addresses across the threads that own its rows.
+#define ZD(i, j) Zd[(long long)(j) * ld + (i)]
 
 __global__ void __launch_bounds__(kThreads) schur_ds_kernel(const __grid_constant__ SchurBatch batch) {
   const SchurJob& J = batch.job[blockIdx.x];
@@ -118,9 +130,10 @@ __global__ void __launch_bounds__(kThreads) schur_ds_kernel(const __grid_constan
   __shared__ dc sv[1024];
   __shared__ RotD srot;
   __shared__ RotD s_rot2[2];
-  __shared__ dc s_hand[2][3];
+  __shared__ dc s_hand[2][4];
   __shared__ int s_flag;
   __shared__ int s_l;
+  __shared__ dc s_mu;
   __shared__ int s_sel[1024];
   const int tid = threadIdx.x;
   if (m > 1024) {
@@ -182,17 +195,19 @@ __global__ void __launch_bounds__(kThreads) schur_ds_kernel(const __grid_constan
     for (int i = c + 1 + tid; i < m; i += blockDim.x) HD(i, c) = (i == c + 1) ? alpha : czero();
     // H <- H P and Z <- Z P: one thread per row of H and per row of Z
     for (int t = tid; t < 2 * m; t += blockDim.x) {
-      dc* row = (t < m) ? &HD(t, 0) : &ZD(t - m, 0);
+      const bool isz = t >= m;
+      dc* row = isz ? &ZD(t - m, 0) : &HD(t, 0);
+      const long long st = isz ? ld : 1;
       dc u0 = czero(), u1 = czero();
       int j = c + 1;
       for (; j + 1 < m; j += 2) {
-        const dc x0 = row[j], x1 = row[j + 1];
+        const dc x0 = row[j * st], x1 = row[(j + 1) * st];
         u0 = cadd(u0, cmul(x0, sv[j]));
         u1 = cadd(u1, cmul(x1, sv[j + 1]));
       }
-      if (j < m) u0 = cadd(u0, cmul(row[j], sv[j]));
+      if (j < m) u0 = cadd(u0, cmul(row[j * st], sv[j]));
       const dc u = cscale(cadd(u0, u1), tau);
-      for (j = c + 1; j < m; ++j) row[j] = csub(row[j], cmul(u, cconj(sv[j])));
+      for (j = c + 1; j < m; ++j) row[j * st] = csub(row[j * st], cmul(u, cconj(sv[j])));
     }
     __syncthreads();
   }
@@ -227,135 +242,207 @@ __global__ void __launch_bounds__(kThreads) schur_ds_kernel(const __grid_constan
         status = 1;
         break;
       }
-      dc mu;
-      if (its % 10 == 0) {
-        const dc hs = HD(ihi, ihi - 1);
-        mu = cadd(HD(ihi, ihi), dc{df{0.75f * fabsf(approx(hs.re)), 0.f}, dfz()});
-      } else {
-        // Wilkinson shift, once per iteration, evaluated in FP64
-        const double2 a = cto(HD(ihi - 1, ihi - 1)), bq = cto(HD(ihi - 1, ihi)), cq = cto(HD(ihi, ihi - 1)),
-                      d = cto(HD(ihi, ihi));
-        const double2 tr2 = swi::cscale(swi::csub(a, d), 0.5);
-        const double2 bc = swi::cmul(bq, cq);
-        const double2 disc = csqrt_p(swi::cadd(swi::cmul(tr2, tr2), bc));
-        const double2 r1 = swi::cadd(tr2, disc), r2 = swi::csub(tr2, disc);
-        const double2 den = swi::cabs(r1) >= swi::cabs(r2) ? r1 : r2;
-        const double2 m64 = swi::cabs(den) > 0.0 ? swi::csub(d, swi::cdiv(bc, den)) : d;
-        mu = cfrom(m64);
+      if (tid == 0) {  // the shift, formed once and shared
+        dc mu;
+        if (its % 10 == 0) {
+          const dc hs = HD(ihi, ihi - 1);
+          mu = cadd(HD(ihi, ihi), dc{df{0.75f * fabsf(approx(hs.re)), 0.f}, dfz()});
+        } else {
+          // Wilkinson shift, evaluated in FP64
+          const double2 a = cto(HD(ihi - 1, ihi - 1)), bq = cto(HD(ihi - 1, ihi)), cq = cto(HD(ihi, ihi - 1)),
+                        d = cto(HD(ihi, ihi));
+          const double2 tr2 = swi::cscale(swi::csub(a, d), 0.5);
+          const double2 bc = swi::cmul(bq, cq);
+          const double2 disc = csqrt_p(swi::cadd(swi::cmul(tr2, tr2), bc));
+          const double2 r1 = swi::cadd(tr2, disc), r2 = swi::csub(tr2, disc);
+          const double2 den = swi::cabs(r1) >= swi::cabs(r2) ? r1 : r2;
+          const double2 m64 = swi::cabs(den) > 0.0 ? swi::csub(d, swi::cdiv(bc, den)) : d;
+          mu = cfrom(m64);
+        }
+        s_mu = mu;
       }
       __syncthreads();
-      if (m + 32 <= (int)blockDim.x) {
-        // One barrier per rotation.  Thread 0 chases the bulge: it updates the
-        // 2x2 block, column k-1 and row k+2, and computes the next rotation from
-        // values it produced itself.  Thread 32+q owns column q (left updates,
-        // rows k, k+1), row q (right updates, columns k, k+1) and row q of Z,
-        // keeps its pair in registers and prefetches the next one.  The two
-        // values that change hands each step go through double-buffered shared
-        // slots: H[k+1][k+2] (column owner -> thread 0) and H[k][k+1], H[k][k+2]
-        // (-> the owner of row k, which joins the right updates next step).
-        const int q = tid - 32;
-        const bool owner = tid >= 32 && q < m;
+      const dc mu = s_mu;
+      if (m <= kMaxOwners) {
+        // One barrier per rotation.  Warp 0 chases the bulge: at step k its
+        // lanes 0-6 each form one half-rotation h = c u + w v (w = +-s or
+        // +-conj(s)) of the 2x2 block {k, k+1}, of row k+2 (the new bulge) and
+        // of column k-1; lanes 0-3 then apply the column rotation to the 2x2
+        // block and every lane forms the next rotation from H[k+1][k] and the
+        // bulge.  Owner q (owner_index) holds column q (left updates, rows k, k+1), row q
+        // (right updates, columns k, k+1) and row q of Z, with its pair in
+        // registers and the next-but-one element prefetched.  Hand-offs through
+        // double-buffered shared slots, written at step k and read at k+1:
+        // [0] H[k+1][k+2] (owner of column k+2 -> lanes 1, 3), [1] H[k][k+1]
+        // (lane 3 -> owner of row k, which joins the right updates), [2]
+        // H[k][k+2] and [3] H[k][k+3] (owners of columns k+2, k+3 -> owner of
+        // row k).  Diagonal and subdiagonal entries ahead of the bulge come from
+        // a copy in shared memory taken before the sweep.
+        dc* sdg = sv;        // H[i][i]
+        dc* ssb = sv + 512;  // H[i+1][i]
+        for (int i = l + tid; i <= ihi; i += blockDim.x) {
+          sdg[i] = HD(i, i);
+          if (i < ihi) ssb[i] = HD(i + 1, i);
+        }
+        const int q = owner_index(tid);
+        const bool owner = q >= 0 && q < m;
+        const int ln = tid & 31;
         dc lt = czero(), lb = czero(), rl = czero(), rr = czero(), zl = czero(), zr = czero();
-        dc p_kk = czero(), p_kk1 = czero(), p_k1k = czero(), p_k1k1 = czero(), p_k2k1 = czero();
-        dc p_x = czero(), p_y = czero();
+        dc pl0 = czero(), pl1 = czero(), pr0 = czero(), pr1 = czero(), pz0 = czero(), pz1 = czero();
+        dc pu = czero(), pv = czero();
+        // half-rotation coefficient signs: w = (sr Re s, si Im s)
+        float sr1 = 1.f, si1 = 1.f, sr2 = 1.f, si2 = 1.f;
+        if (ln <= 1) sr1 = -1.f;
+        if (ln == 4 || ln == 5) si1 = -1.f;
+        if (ln == 5) sr1 = -1.f;
+        if (ln == 0 || ln == 2) si2 = -1.f;
+        if (ln == 1 || ln == 3) { sr2 = -1.f; si2 = -1.f; }
         if (owner) {
+          const bool m2 = l + 2 < m;
           if (q >= l + 2) {
             lt = HD(l, q);
             lb = HD(l + 1, q);
+            if (m2) pl0 = HD(l + 2, q);
           }
           if (q < l) {
             rl = HD(q, l);
             rr = HD(q, l + 1);
+            if (m2) pr0 = HD(q, l + 2);
           }
           zl = ZD(q, l);
           zr = ZD(q, l + 1);
+          if (m2) pz0 = ZD(q, l + 2);
         }
-        if (tid == 0) {
-          p_kk = HD(l, l);
-          p_kk1 = HD(l, l + 1);
-          p_k1k = HD(l + 1, l);
-          p_k1k1 = HD(l + 1, l + 1);
-          p_k2k1 = (l + 2 <= ihi) ? HD(l + 2, l + 1) : czero();
-          s_rot2[l & 1] = make_rot_ds(csub(p_kk, mu), p_k1k);
+        if (tid < 32) {
+          const dc a = HD(l, l), b = HD(l, l + 1), c = HD(l + 1, l), d = HD(l + 1, l + 1);
+          const dc f0 = (l + 2 <= ihi) ? HD(l + 2, l + 1) : czero();
+          if (ln == 0) { pu = c; pv = a; }
+          if (ln == 1) { pu = d; pv = b; }
+          if (ln == 2) { pu = a; pv = c; }
+          if (ln == 3) { pu = b; pv = d; }
+          if (ln == 4) pv = f0;
+          if (ln == 5) pu = f0;
+          const RotD g0 = make_rot_ds(csub(a, mu), c);
+          if (ln == 0) s_rot2[l & 1] = g0;
         }
         __syncthreads();
-        for (int k = l; k < ihi; ++k) {
+        // one step; (pa, pb) are the prefetch slots consumed / refilled
+        auto step = [&](const int k, dc& pla, dc& plb, dc& pra, dc& prb, dc& pza, dc& pzb) {
           const RotD g = s_rot2[k & 1];
           const int par = k & 1;
-          if (tid == 0) {
-            // operands of the next step first: final since the last barrier
-            dc n_k1k1 = czero(), n_k2k1 = czero();
-            if (k + 1 < ihi) {
-              n_k1k1 = HD(k + 2, k + 2);
-              if (k + 3 <= ihi) n_k2k1 = HD(k + 3, k + 2);
-            }
-            n_upd += (m - ((k == l) ? l : k - 1)) + (min(k + 2, ihi) + 1) + m;
+          if (tid < 32) {
+            if (ln == 0) n_upd += (m - ((k == l) ? l : k - 1)) + (min(k + 2, ihi) + 1) + m;
             if (k > l) {
-              p_kk1 = s_hand[par ^ 1][0];  // H[k][k+1] from the owner of column k+1
-              dc tx = p_x, ty = p_y;       // column k-1: (H[k][k-1], H[k+1][k-1]) -> (r, 0)
-              rot_rows(tx, ty, g);
-              HD(k, k - 1) = tx;
-              HD(k + 1, k - 1) = czero();
+              const dc hb = s_hand[par ^ 1][0];  // H[k][k+1]
+              if (ln == 1) pv = hb;
+              if (ln == 3) pu = hb;
             }
-            dc a = p_kk, b = p_kk1, c = p_k1k, d = p_k1k1;
-            rot_rows(a, c, g);
-            rot_rows(b, d, g);
-            rot_cols(a, b, g);
-            rot_cols(c, d, g);
-            HD(k, k) = a;
-            HD(k, k + 1) = b;
-            HD(k + 1, k) = c;
-            HD(k + 1, k + 1) = d;
-            s_hand[par][1] = b;  // H[k][k+1] for the owner of row k
-            dc e = czero(), f = p_k2k1;
-            if (k + 2 <= ihi) {
-              rot_cols(e, f, g);  // row k+2: (0, H[k+2][k+1]) -> the new bulge and subdiagonal
-              HD(k + 2, k) = e;
-              HD(k + 2, k + 1) = f;
+            // lane-dependent selections above and below: reconverge the warp
+            // before each stretch of arithmetic so that it issues once for all lanes
+            __syncwarp();
+            const dc w1 = dc{df{sr1 * g.s.re.h, sr1 * g.s.re.l}, df{si1 * g.s.im.h, si1 * g.s.im.l}};
+            const dc h1 = cadd(cscale(pu, g.c), cmul(w1, pv));
+            dc o;
+            o.re.h = __shfl_xor_sync(0xffffffffu, h1.re.h, 1);
+            o.re.l = __shfl_xor_sync(0xffffffffu, h1.re.l, 1);
+            o.im.h = __shfl_xor_sync(0xffffffffu, h1.im.h, 1);
+            o.im.l = __shfl_xor_sync(0xffffffffu, h1.im.l, 1);
+            const dc w2 = dc{df{sr2 * g.s.re.h, sr2 * g.s.re.l}, df{si2 * g.s.im.h, si2 * g.s.im.l}};
+            const dc h2 = cadd(cscale(h1, g.c), cmul(w2, o));
+            dc cpp, ep;  // H[k+1][k] and the bulge H[k+2][k], broadcast
+            cpp.re.h = __shfl_sync(0xffffffffu, h2.re.h, 0);
+            cpp.re.l = __shfl_sync(0xffffffffu, h2.re.l, 0);
+            cpp.im.h = __shfl_sync(0xffffffffu, h2.im.h, 0);
+            cpp.im.l = __shfl_sync(0xffffffffu, h2.im.l, 0);
+            ep.re.h = __shfl_sync(0xffffffffu, h1.re.h, 4);
+            ep.re.l = __shfl_sync(0xffffffffu, h1.re.l, 4);
+            ep.im.h = __shfl_sync(0xffffffffu, h1.im.h, 4);
+            ep.im.l = __shfl_sync(0xffffffffu, h1.im.l, 4);
+            // lanes 0, 2 need H[k+2][k+1] (lane 5) and H[k+1][k+1] (lane 1)
+            const int src_u = (ln == 0) ? 5 : 1, src_v = (ln == 0) ? 1 : 5;
+            dc nu, nv;
+            nu.re.h = __shfl_sync(0xffffffffu, (ln == 5) ? h1.re.h : h2.re.h, src_u);
+            nu.re.l = __shfl_sync(0xffffffffu, (ln == 5) ? h1.re.l : h2.re.l, src_u);
+            nu.im.h = __shfl_sync(0xffffffffu, (ln == 5) ? h1.im.h : h2.im.h, src_u);
+            nu.im.l = __shfl_sync(0xffffffffu, (ln == 5) ? h1.im.l : h2.im.l, src_u);
+            nv.re.h = __shfl_sync(0xffffffffu, (ln == 5) ? h1.re.h : h2.re.h, src_v);
+            nv.re.l = __shfl_sync(0xffffffffu, (ln == 5) ? h1.re.l : h2.re.l, src_v);
+            nv.im.h = __shfl_sync(0xffffffffu, (ln == 5) ? h1.im.h : h2.im.h, src_v);
+            nv.im.l = __shfl_sync(0xffffffffu, (ln == 5) ? h1.im.l : h2.im.l, src_v);
+            {
+              // lane 0: H[k+1][k], 1: H[k+1][k+1], 2: H[k][k], 3: H[k][k+1],
+              // 4, 5: H[k+2][k], H[k+2][k+1], 6: H[k][k-1] (and H[k+1][k-1] = 0)
+              int r = -1, cc = 0;
+              if (ln == 0) { r = k + 1; cc = k; }
+              if (ln == 1) { r = k + 1; cc = k + 1; }
+              if (ln == 2) { r = k; cc = k; }
+              if (ln == 3) { r = k; cc = k + 1; }
+              if (ln == 4 && k + 2 <= ihi) { r = k + 2; cc = k; }
+              if (ln == 5 && k + 2 <= ihi) { r = k + 2; cc = k + 1; }
+              if (ln == 6 && k > l) { r = k; cc = k - 1; }
+              if (ln == 7 && k > l) { r = k + 1; cc = k - 1; }
+              const dc val = (ln <= 3) ? h2 : ((ln == 7) ? czero() : h1);
+              if (r >= 0) HD(r, cc) = val;
+              if (ln == 3) s_hand[par][1] = h2;
             }
+            __syncwarp();
             if (k + 1 < ihi) {
-              s_rot2[par ^ 1] = make_rot_ds(c, e);
-              p_x = c;
-              p_y = e;
-              p_kk = d;
-              p_k1k = f;
-              p_k1k1 = n_k1k1;
-              p_k2k1 = n_k2k1;
+              const RotD gn = make_rot_ds(cpp, ep);
+              if (ln == 0) s_rot2[par ^ 1] = gn;
+              const dc dg = sdg[k + 2];
+              const dc sb = (k + 3 <= ihi) ? ssb[k + 2] : czero();
+              if (ln == 0 || ln == 2) { pu = nu; pv = nv; }
+              if (ln == 1) pu = dg;
+              if (ln == 3) pv = dg;
+              if (ln == 4) { pu = czero(); pv = sb; }
+              if (ln == 5) { pu = sb; pv = czero(); }
+              if (ln == 6) { pu = cpp; pv = ep; }
             }
+            __syncwarp();
           } else if (owner) {
-            const bool more = k + 2 < m;
-            const dc n_lb = (more && q >= k + 2) ? HD(k + 2, q) : czero();
-            const dc n_rr = (more && q < k) ? HD(q, k + 2) : czero();
-            const dc n_zr = more ? ZD(q, k + 2) : czero();
+            const bool m3 = k + 3 < m;
             if (q >= k + 2) {  // left: rows k, k+1 of column q
+              if (m3 && q >= k + 4) plb = HD(k + 3, q);
               rot_rows(lt, lb, g);
-              HD(k, q) = lt;
-              HD(k + 1, q) = lb;
+              HD(k, q) = lt;  // final for this sweep; H[k+1][q] stays in a register
               if (q == k + 2) {
-                s_hand[par][0] = lb;  // H[k+1][k+2] for thread 0
+                s_hand[par][0] = lb;  // H[k+1][k+2] for warp 0
                 s_hand[par][2] = lt;  // H[k][k+2] for the owner of row k
               }
+              if (q == k + 3) s_hand[par][3] = lt;  // H[k][k+3] for the owner of row k
               lt = lb;
-              lb = n_lb;
+              lb = pla;
             }
             if (q < k) {  // right: columns k, k+1 of row q
               if (q == k - 1 && k > l) {
                 rl = s_hand[par ^ 1][1];
                 rr = s_hand[par ^ 1][2];
+                pra = s_hand[par ^ 1][3];
               }
+              if (m3) prb = HD(q, k + 3);
               rot_cols(rl, rr, g);
               HD(q, k) = rl;
-              HD(q, k + 1) = rr;
               rl = rr;
-              rr = n_rr;
+              rr = pra;
             }
+            if (m3) pzb = ZD(q, k + 3);
             rot_cols(zl, zr, g);  // Z: columns k, k+1 of row q
             ZD(q, k) = zl;
-            ZD(q, k + 1) = zr;
             zl = zr;
-            zr = n_zr;
+            zr = pza;
           }
           __syncthreads();
+        };
+        int k = l;
+        for (; k + 1 < ihi; k += 2) {
+          step(k, pl0, pl1, pr0, pr1, pz0, pz1);
+          step(k + 1, pl1, pl0, pr1, pr0, pz1, pz0);
+        }
+        if (k < ihi) step(k, pl0, pl1, pr0, pr1, pz0, pz1);
+        if (owner) {  // the elements still held in registers
+          if (q >= ihi + 1) HD(ihi, q) = lt;
+          if (q < ihi - 1) HD(q, ihi) = rl;
+          ZD(q, ihi) = zl;
         }
       } else
       for (int k = l; k < ihi; ++k) {
@@ -440,17 +527,17 @@ __global__ void __launch_bounds__(kThreads) schur_ds_kernel(const __grid_constan
   const int kk = s_flag;
   for (int i = tid; i < m; i += blockDim.x) s_sel[i] = (s_sel[i] < kk) ? 1 : 0;
   __syncthreads();
-  if (m + 32 <= (int)blockDim.x) {
+  if (m <= kMaxOwners) {
     // Each selected eigenvalue lambda moves up from pos to ks by adjacent swaps
     // q = pos-1, ..., ks, one barrier per swap.  The rotation of swap q comes
     // from (T[q][q+1], lambda - T[q][q]); the next one needs T[q-1][q] after
     // the column update of row q-1, so thread 0 updates row q-1 itself and
-    // forms the next rotation at once.  Thread 32+i owns column i (rows q, q+1),
+    // forms the next rotation at once.  Owner i (owner_index) holds column i (rows q, q+1),
     // row i (columns q, q+1) for i < q-1 and row i of Z, with its pair in
     // registers.  Hand-offs: T[q-1][q+1] (thread 0 -> the owner of column q+1,
     // which joins next swap) and T[q-2][q] (owner of row q-2 -> thread 0).
-    const int i = tid - 32;
-    const bool owner = tid >= 32 && i < m;
+    const int i = owner_index(tid);
+    const bool owner = i >= 0 && i < m;
     int ks = 0;
     for (int pos = 0; pos < m; ++pos) {
       if (!s_sel[pos]) continue;
@@ -513,26 +600,28 @@ __global__ void __launch_bounds__(kThreads) schur_ds_kernel(const __grid_constan
             if (i >= q + 2) {  // rows q, q+1 of column i
               if (i == q + 2 && q < q0) lt = s_hand[par ^ 1][0];
               rot_rows(lt, lb, g);
-              HD(q, i) = lt;
-              HD(q + 1, i) = lb;
+              HD(q + 1, i) = lb;  // final for this bubble; T[q][i] stays in a register
               lb = lt;
               lt = n_lt;
             }
             if (i < q - 1) {  // columns q, q+1 of row i
               rot_cols(rl, rr, g);
-              HD(i, q) = rl;
               HD(i, q + 1) = rr;
               if (i == q - 2) s_hand[par][1] = rl;  // T[q-2][q] for thread 0
               rr = rl;
               rl = n_rl;
             }
             rot_cols(zl, zr, g);
-            ZD(i, q) = zl;
             ZD(i, q + 1) = zr;
             zr = zl;
             zl = n_zl;
           }
           __syncthreads();
+        }
+        if (owner) {  // the elements still held in registers
+          if (i >= ks + 2) HD(ks, i) = lb;
+          if (i < ks - 1) HD(i, ks) = rr;
+          ZD(i, ks) = zr;
         }
         if (tid == 0) {
           s_sel[ks] = 1;

@@ -49,6 +49,10 @@ MATVEC_BUDGET = 8192
 # FP64 peak of GB300 derived from unit counts and clocks: 152 SMs x 2 FP64 FMA
 # per SM clock x 2 flops x the sampled SM clock (nominal 1.25 TFLOP/s at 2.07 GHz).
 FP64_FLOPS_PER_CLK = 152 * 2 * 2
+# DRAM bytes (read + write) of one launch of the double-single Schur kernel,
+# from an ncu capture of the lowest window's first restart (m = 229); the
+# m x m work arrays stay in L2.  None once the kernel changes.
+SCHUR_DRAM_BYTES = 1.627648e6 + 0.062464e6
 
 
 def _env_int(name, default):
@@ -89,7 +93,7 @@ def plan(cfg, ctx=None, wire=None):
     """8 equal-width windows over the estimated lowest n_r real parts, and the energy grid.
 
     The estimate is the committed Kohn-Sham spectrum of the workload (H_KS
-    alone, first-order estimate of Re eps, Section 2.2.2) when present,
+    alone, first-order estimate of Re eps, Section 2, Eq. 5) when present,
     otherwise a marching pre-solve on the GPU.
     """
     n_r = cfg["n_r"]
@@ -359,7 +363,8 @@ def main():
     if dom == "schur":
         per_cta = rate("schur")  # each launch is one CTA on one SM
         roof = {"kernel": "schur", "bound": "alu", "achieved": per_cta, "peak": ds_rot_peak_cta,
-                "unit": "TFLOP/s per CTA", "frac": per_cta / ds_rot_peak_cta, "traffic": None,
+                "unit": "TFLOP/s per CTA", "frac": per_cta / ds_rot_peak_cta, "traffic": SCHUR_DRAM_BYTES,
+                "traffic_unit": "bytes per launch (ncu, lowest window)",
                 "peak_source": "derived: one SM's FP32 issue (128/clk x sampled clock) / 60 instructions per "
                                "20-flop double-single Givens pair update",
                 "note": "one CTA per window on a side stream; latency-bound chain of dependent Givens "

@@ -2,7 +2,7 @@
 
 The paper places its shifts with foreknowledge of the spectrum and suggests
 estimating it from the lowest eigenvalues of H_KS alone (without i Gamma),
-which approximate Re eps_k to first order (Section 2.2.2, Eq. (5)).  This
+which approximate Re eps_k to first order (Section 2, Eq. (5)).  This
 script computes the lowest `count` eigenvalues of the real symmetric H of a
 workload with the oracle's stencil (Gamma = 0) and ARPACK's Lanczos driver,
 and writes them, one per line, to tests/golden/<name>_ks_spectrum.txt.

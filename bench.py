@@ -201,6 +201,44 @@ def cpu_baseline(cfg, sigma1=None):
             "seconds": dt}
 
 
+def stencil_c64_rate(swi, stream, hbm, launches=20, warm=3):
+    """The complex64 stencil of the reduced-precision form on its own 96x96x192 grid, 16 columns.
+
+    X and Y (226 MB each) exceed L2; the device time of `launches` back-to-back
+    launches is taken with CUDA events on the launching stream.  Bytes are the
+    algorithmic ones: read X, write Y (16 B per grid point per column) plus the
+    FP32 V and Gamma (8 B per grid point).
+    """
+    import torch
+    w = W.config_wire("wire_96x96x192")
+    nvec = 16
+    ctx = swi.Context(w.nx, w.ny, w.nz, w.h, stream=stream.cuda_stream)
+    ctx.set_potential(w.V)
+    ctx.set_absorber(w.gamma_L, w.gamma_R)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(5)
+    X = torch.randn((w.N, nvec), dtype=torch.complex64, device="cuda", generator=g)
+    sig = np.linspace(-1.0, 0.5, nvec).astype(np.float32)
+    for _ in range(warm):
+        Y = ctx.apply_c64(X, sig)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(launches):
+        Y = ctx.apply_c64(X, sig)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / launches
+    byts = (16.0 * nvec + 8.0) * w.N
+    ctx.close()
+    del X, Y
+    gbs = byts / (ms / 1e3) / 1e9
+    return {"kernel": "stencil_c64_kernel", "grid": [w.nx, w.ny, w.nz], "columns": nvec, "ms_per_launch": ms,
+            "bytes_per_launch": byts, "GB/s": gbs, "hbm_peak_GB/s": hbm, "frac_of_hbm": gbs / hbm,
+            "note": "complex64 vectors, FP32 arithmetic (the reduced-precision operator); not part of the "
+                    "FP64 step; inputs larger than L2"}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -416,6 +454,8 @@ def main():
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    log("complex64 stencil")
+    out["stencil_c64"] = stencil_c64_rate(swi, stream, hbm)
     if not args.no_cpu_baseline:
         log("cpu baseline")
         out["cpu_baseline"] = cpu_baseline(cfg, float(sig[0]))

@@ -159,6 +159,17 @@ swi_status swi_plan_windows(swi_ctx* ctx, int n_r, int p, double e_min, double e
 swi_status swi_apply(swi_ctx* ctx, int nvec, const double* sigma, const void* X, void* Y,
                      int on_device);
 
+/* The same shifted operator on complex64 vectors with FP32 arithmetic (the
+ * operator of the reduced-precision form): Y[:, c] = (A - sigma[c]) X[:, c],
+ * X and Y complex64 [N][nvec] (interleaved re, im floats), sigma a host array
+ * of nvec floats; V and Gamma are used as FP32 copies.  Error relative to the
+ * FP64 operator: FP32 rounding of ~40 terms.  With on_device != 0, X and Y are
+ * device pointers and the call returns without synchronising the context's
+ * stream (the kernel is ordered on it); otherwise they are host arrays and the
+ * call returns when Y is written.  Errors: SWI_EINVAL, SWI_ESTATE, SWI_ECUDA. */
+swi_status swi_apply_c64(swi_ctx* ctx, int nvec, const float* sigma, const void* X, void* Y,
+                         int on_device);
+
 /* Solve all windows (batched on the device), merge them with Algorithm 2,
  * keep the lowest-real-part pairs and scale them to U^T U = I.
  * opts may be NULL (defaults); info may be NULL.

@@ -85,6 +85,7 @@ struct swi_ctx {
   double h = 0.0;
   int bc = SWI_BC_ODD, precision = SWI_PREC_F64;
   DevMem V, G, gL, gR;
+  DevMem V32, G32;  // FP32 copies for the complex64 stencil
   bool has_V = false, has_G = false;
   double maxabsV = 0.0, maxG = 0.0;
   std::vector<double> sigma;
@@ -837,6 +838,11 @@ swi_status swi_set_potential(swi_ctx* c, const double* V, int on_device) {
     double mx = 0.0;
     for (double v : h) mx = std::max(mx, std::fabs(v));
     copy_in(c->V, h.data(), sizeof(double) * n, false, c->stream);
+    {
+      std::vector<float> f(h.begin(), h.end());
+      copy_in(c->V32, f.data(), sizeof(float) * n, false, c->stream);
+      sync(c->stream);
+    }
     sync(c->stream);
     c->maxabsV = mx;
     c->has_V = true;
@@ -866,6 +872,11 @@ swi_status swi_set_absorber(swi_ctx* c, const double* gL, const double* gR, int 
     copy_in(c->gL, l.data(), sizeof(double) * n, false, c->stream);
     copy_in(c->gR, r.data(), sizeof(double) * n, false, c->stream);
     copy_in(c->G, g.data(), sizeof(double) * n, false, c->stream);
+    {
+      std::vector<float> f(g.begin(), g.end());
+      copy_in(c->G32, f.data(), sizeof(float) * n, false, c->stream);
+      sync(c->stream);
+    }
     sync(c->stream);
     c->maxG = mx;
     c->has_G = true;
@@ -944,6 +955,40 @@ swi_status swi_apply(swi_ctx* c, int nvec, const double* sigma, const void* X, v
     dy.ensure(bytes);
     SWI_CUDA_TRY(cudaMemcpyAsync(dx.p, X, bytes, cudaMemcpyHostToDevice, c->stream));
     apply_block(c, dx.as<double2>(), nvec, dy.as<double2>(), nvec, nvec);
+    SWI_CUDA_TRY(cudaMemcpyAsync(Y, dy.p, bytes, cudaMemcpyDeviceToHost, c->stream));
+    sync(c->stream);
+    return SWI_OK;
+  });
+}
+
+swi_status swi_apply_c64(swi_ctx* c, int nvec, const float* sigma, const void* X, void* Y, int on_device) {
+  return guarded(c, [&]() -> swi_status {
+    if (nvec < 1 || !sigma || !X || !Y) return fail(c, SWI_EINVAL, "bad arguments");
+    if (!c->has_V || !c->has_G) return fail(c, SWI_ESTATE, "potential and absorbers must be set");
+    const size_t bytes = sizeof(float2) * (size_t)c->N * nvec;
+    c->sig_dev.ensure(sizeof(float) * std::max(nvec, 64));
+    SWI_CUDA_TRY(cudaMemcpyAsync(c->sig_dev.p, sigma, sizeof(float) * nvec, cudaMemcpyHostToDevice, c->stream));
+    swi::StencilC64Params P;
+    P.nx = c->nx;
+    P.ny = c->ny;
+    P.nz = c->nz;
+    P.bc = c->bc;
+    for (int m = 0; m < 7; ++m) P.cm[m] = (float)(-kFD[m] / (2.0 * c->h * c->h));
+    P.V = c->V32.as<float>();
+    P.G = c->G32.as<float>();
+    const double Nn = (double)c->N;
+    if (on_device) {
+      ProfScope ps(c, SWI_K_STENCIL, kStencilFlops * Nn * nvec, (16.0 * nvec + 8.0) * Nn);
+      swi::launch_stencil_c64(P, static_cast<const float2*>(X), nvec, static_cast<float2*>(Y), nvec, nvec,
+                              c->sig_dev.as<float>(), c->stream, &c->launches);
+      return SWI_OK;
+    }
+    DevMem dx, dy;
+    dx.ensure(bytes);
+    dy.ensure(bytes);
+    SWI_CUDA_TRY(cudaMemcpyAsync(dx.p, X, bytes, cudaMemcpyHostToDevice, c->stream));
+    swi::launch_stencil_c64(P, dx.as<float2>(), nvec, dy.as<float2>(), nvec, nvec, c->sig_dev.as<float>(), c->stream,
+                            &c->launches);
     SWI_CUDA_TRY(cudaMemcpyAsync(Y, dy.p, bytes, cudaMemcpyDeviceToHost, c->stream));
     sync(c->stream);
     return SWI_OK;

@@ -93,6 +93,17 @@ struct StencilBlock {
   int sigma_off;      // index into the sigma table of column 0
 };
 
+// complex64 form (FP32 arithmetic), one block of columns
+struct StencilC64Params {
+  int nx, ny, nz;
+  int bc;
+  float cm[7];       // -c_m / (2 h^2)
+  const float* V;    // N
+  const float* G;    // Gamma_L + Gamma_R, N
+};
+void launch_stencil_c64(const StencilC64Params& P, const float2* X, int ldx, float2* Y, int ldy, int ncols,
+                        const float* sigma_dev, cudaStream_t s, long long* launches);
+
 constexpr int kMaxBatch = 64;
 
 struct StencilBatch {

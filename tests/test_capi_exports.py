@@ -14,7 +14,7 @@ def _declared():
     with open(os.path.join(ROOT, "include", "swi.h")) as f:
         text = f.read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(swi_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(swi_[a-z0-9_]+)\s*\(", text)))
 
 
 @pytest.fixture(scope="module")

@@ -90,6 +90,45 @@ def test_stencil_device_pointers(swi):
     assert np.array_equal(Yd.cpu().numpy(), Yh)
 
 
+# complex64 stencil: FP32 rounding of ~40 terms whose magnitudes sum to at most
+# ||A||_G max|x| (Gershgorin), plus the FP32 copies of V, Gamma, sigma and the
+# weights: |Y - Y_FP64| <= 40 * 2^-24 * ||A||_G max|X| ~ 2.4e-6 ||A||_G max|X|.
+C64_TOL = 3e-6
+
+
+def _c64_case(swi, w, nvec, bc, seed, device=False):
+    rng = np.random.default_rng(seed)
+    X = (rng.standard_normal((w.N, nvec)) + 1j * rng.standard_normal((w.N, nvec))).astype(np.complex64)
+    sig = rng.uniform(-2, 2, nvec).astype(np.float32)
+    with _ctx(swi, w, bc) as c:
+        if device:
+            import torch
+            Y = c.apply_c64(torch.as_tensor(X).cuda(), sig)
+            torch.cuda.synchronize()
+            Y = Y.cpu().numpy()
+        else:
+            Y = c.apply_c64(X, sig)
+    X64 = X.astype(np.complex128)
+    Yo = stencil.apply_A(X64, w.nx, w.ny, w.nz, w.h, w.V, w.gamma_L, w.gamma_R, bc=bc) - X64 * sig[None, :]
+    an = stencil.gershgorin_norm(w.h, w.V, w.gamma_L, w.gamma_R)
+    err = np.max(np.abs(Y - Yo))
+    assert err <= C64_TOL * an * np.max(np.abs(X64)), err
+    return err
+
+
+@pytest.mark.parametrize("shape", [(13, 9, 17), (6, 20, 7), (33, 17, 40)])
+@pytest.mark.parametrize("bc", [0, 1])
+def test_stencil_c64_ragged(swi, shape, bc):
+    # partial 16 x 8 tiles, 5 columns (a partial group of 4), short z chunks
+    _c64_case(swi, W.make_wire(*shape, 0.5, 4, 3), 5, bc, 11)
+
+
+def test_stencil_c64_precision_form_grid(swi):
+    # the 96x96x192 grid of the reduced-precision workload, 16 columns, device pointers
+    w = W.config_wire("wire_96x96x192")
+    _c64_case(swi, w, 16, 0, 12, device=True)
+
+
 # --------------------------------------------------------------------------- solve
 def _solve_vs_dense(swi, w, n_r, p, block, inflate=1.3, extra=4, arith=None):
     A = _dense(w)

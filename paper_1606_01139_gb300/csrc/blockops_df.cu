@@ -619,7 +619,7 @@ void launch_gram_df(const GramBatch& b, int N, const double* w, int bilinear, do
       attr = true;
     }
     const int tiles_i = (maxnx + oz::kTI - 1) / oz::kTI;
-    int nch = (2 * 152 + tiles_i * b.n - 1) / (tiles_i * b.n);
+    int nch = (32 * 152 + tiles_i * b.n - 1) / (tiles_i * b.n);
     nch = std::max(1, std::min(nch, (N + oz::kKC - 1) / oz::kKC));
     while (nch > 1 && (size_t)nch * per_chunk > work_elems) --nch;
     if ((size_t)nch * per_chunk > work_elems) throw Error{SWI_ENOMEM, "gram workspace too small"};
@@ -680,11 +680,14 @@ void launch_rowgemm_df(const RowGemmBatch& b, int N, cudaStream_t s, long long* 
   if (b.n <= 0) return;
   int maxc = 0;
   for (int q = 0; q < b.n; ++q) maxc = b.job[q].ncols > maxc ? b.job[q].ncols : maxc;
-  if (maxc <= 16) {
+  int maxk = 0;
+  for (int q = 0; q < b.n; ++q) maxk = b.job[q].k > maxk ? b.job[q].k : maxk;
+  if (maxc <= 16 && maxk <= 32) {
     dim3 grid((N + 63) / 64, 1, b.n);
     rowgemm_df_kernel<64, 16><<<grid, 256, 0, s>>>(b, N);
   } else if (true) {
-    // wide products (the restart rotation): tensor cores with the exact digit split
+    // long contractions (the Gram-Schmidt update W -= Q C, the restart rotation
+    // Q Z): tensor cores with the exact digit split
     static bool attr = false;
     if (!attr) {
       SWI_CUDA_TRY(

@@ -124,28 +124,42 @@ __global__ void __launch_bounds__(kThreadsC64, 1)
 #pragma unroll
   for (int k = 0; k < 2 * kR + 1; ++k)
     q[k] = mine ? load_z<BC>(X, pt_col, plane_ld, z0 - kR + k, P.nz) : make_float2(0.f, 0.f);
+  const long long prow = (long long)y * P.nx + x;  // point index within a plane
 
   // stage plane z0
-  float2 pre[kSlotsPerThread];
+  float2 preA[kSlotsPerThread], preB[kSlotsPerThread];
 #pragma unroll
   for (int k = 0; k < kSlotsPerThread; ++k)
-    pre[k] = ssg[k] != 0.f ? __ldg(X + (long long)z0 * plane_ld + soff[k]) : make_float2(0.f, 0.f);
+    preA[k] = ssg[k] != 0.f ? __ldg(X + (long long)z0 * plane_ld + soff[k]) : make_float2(0.f, 0.f);
 #pragma unroll
   for (int k = 0; k < kSlotsPerThread; ++k)
-    if (sidx[k] >= 0) sflat[sidx[k]] = make_float2(ssg[k] * pre[k].x, ssg[k] * pre[k].y);
+    if (sidx[k] >= 0) sflat[sidx[k]] = make_float2(ssg[k] * preA[k].x, ssg[k] * preA[k].y);
+  // loads two steps ahead, alternating between the A and B register sets:
+  // staging values of plane z+1 / z+2, queue entries for planes z+7 / z+8,
+  // V and Gamma of planes z / z+1
+#pragma unroll
+  for (int k = 0; k < kSlotsPerThread; ++k)
+    preA[k] = (z0 + 1 < z1 && ssg[k] != 0.f) ? __ldg(X + (long long)(z0 + 1) * plane_ld + soff[k])
+                                             : make_float2(0.f, 0.f);
+  float2 nqA = mine ? load_z<BC>(X, pt_col, plane_ld, z0 + kR + 1, P.nz) : make_float2(0.f, 0.f), nqB;
+  float vA = mine ? __ldg(P.V + (long long)z0 * plane + prow) : 0.f, gA = mine ? __ldg(P.G + (long long)z0 * plane + prow) : 0.f;
+  float vB = 0.f, gB = 0.f;
   __syncthreads();
 
-  for (int z = z0; z < z1; ++z) {
-    // loads for the next step first, so that their latency overlaps this step
-    const float2 nq = mine ? load_z<BC>(X, pt_col, plane_ld, z + kR + 1, P.nz) : make_float2(0.f, 0.f);
-    const bool more = z + 1 < z1;
+  auto step = [&](const int z, float2 (&pcur)[kSlotsPerThread], float2 (&pnxt)[kSlotsPerThread], float2& qcur,
+                  float2& qnxt, float& vcur, float& gcur, float& vnxt, float& gnxt) {
+    const bool more2 = z + 2 < z1;
 #pragma unroll
     for (int k = 0; k < kSlotsPerThread; ++k)
-      pre[k] = (more && ssg[k] != 0.f) ? __ldg(X + (long long)(z + 1) * plane_ld + soff[k]) : make_float2(0.f, 0.f);
+      pnxt[k] = (more2 && ssg[k] != 0.f) ? __ldg(X + (long long)(z + 2) * plane_ld + soff[k]) : make_float2(0.f, 0.f);
+    qnxt = mine ? load_z<BC>(X, pt_col, plane_ld, z + kR + 2, P.nz) : make_float2(0.f, 0.f);
+    if (mine && z + 1 < z1) {
+      vnxt = __ldg(P.V + (long long)(z + 1) * plane + prow);
+      gnxt = __ldg(P.G + (long long)(z + 1) * plane + prow);
+    }
     if (mine) {
-      const long long row = (long long)z * plane + (long long)y * P.nx + x;
-      const float d = 3.f * cm[0] + __ldg(P.V + row) - sig;
-      const float g = __ldg(P.G + row);
+      const float d = 3.f * cm[0] + vcur - sig;
+      const float g = gcur;
       const float2 x0v = q[kR];
       float ar = fmaf(d, x0v.x, g * x0v.y);
       float ai = fmaf(d, x0v.y, -g * x0v.x);
@@ -157,19 +171,25 @@ __global__ void __launch_bounds__(kThreadsC64, 1)
         ar = fmaf(cm[m], (a.x + b.x) + (u.x + w.x) + (lo.x + hi.x), ar);
         ai = fmaf(cm[m], (a.y + b.y) + (u.y + w.y) + (lo.y + hi.y), ai);
       }
-      Y[row * ldy + c] = make_float2(ar, ai);
+      Y[((long long)z * plane + prow) * ldy + c] = make_float2(ar, ai);
     }
 #pragma unroll
     for (int k = 0; k < 2 * kR; ++k) q[k] = q[k + 1];
-    q[2 * kR] = nq;
+    q[2 * kR] = qcur;
     __syncthreads();  // every read of plane z is done
-    if (more) {
+    if (z + 1 < z1) {
 #pragma unroll
       for (int k = 0; k < kSlotsPerThread; ++k)
-        if (sidx[k] >= 0) sflat[sidx[k]] = make_float2(ssg[k] * pre[k].x, ssg[k] * pre[k].y);
+        if (sidx[k] >= 0) sflat[sidx[k]] = make_float2(ssg[k] * pcur[k].x, ssg[k] * pcur[k].y);
     }
     __syncthreads();
+  };
+  int z = z0;
+  for (; z + 1 < z1; z += 2) {
+    step(z, preA, preB, nqA, nqB, vA, gA, vB, gB);
+    step(z + 1, preB, preA, nqB, nqA, vB, gB, vA, gA);
   }
+  if (z < z1) step(z, preA, preB, nqA, nqB, vA, gA, vB, gB);
 }
 
 }  // namespace

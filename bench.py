@@ -455,8 +455,9 @@ def main():
         "stencil": {"GB/s": stencil_gbs, "hbm_peak_GB/s": hbm,
                     "frac_of_hbm": (stencil_gbs / hbm) if stencil_gbs else None,
                     "TFLOP/s": rate("stencil"), "fp64_peak_TFLOP/s": fp64_peak,
-                    "frac_of_fp64": rate("stencil") / fp64_peak,
-                    "note": "complex128 stencil: 116 FP64 flops per 32 B, bound by the FP64 pipe"},
+                    "note": "complex128 stencil in double-single arithmetic on the FP32 pipes (116 FP64-class "
+                            "flops per 32 B of vectors); the native-FP64 kernel is capped by the FP64 pipe near "
+                            "0.22 TB/s"},
         "kernels": breakdown,
         "solve": {k: infos[-1][k] for k in ("n_pairs", "n_converged", "n_duplicates", "n_holes", "matvecs",
                                            "max_rel_res", "t_krylov_s", "t_merge_s", "status")},

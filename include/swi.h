@@ -159,6 +159,13 @@ swi_status swi_plan_windows(swi_ctx* ctx, int n_r, int p, double e_min, double e
 swi_status swi_apply(swi_ctx* ctx, int nvec, const double* sigma, const void* X, void* Y,
                      int on_device);
 
+/* swi_apply in double-single arithmetic (the operator of the double-single
+ * Krylov loop): same arguments, complex128 in and out; every input value is
+ * split into two floats and each of the 37 terms is an exact FMA product
+ * summed with TwoSum, ~2^-48 relative per term.  Errors as swi_apply. */
+swi_status swi_apply_ds(swi_ctx* ctx, int nvec, const double* sigma, const void* X, void* Y,
+                        int on_device);
+
 /* The same shifted operator on complex64 vectors with FP32 arithmetic (the
  * operator of the reduced-precision form): Y[:, c] = (A - sigma[c]) X[:, c],
  * X and Y complex64 [N][nvec] (interleaved re, im floats), sigma a host array

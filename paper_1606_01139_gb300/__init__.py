@@ -26,7 +26,7 @@ ARITH_DS, ARITH_F64 = 2, 1
 
 # Every entry point declared in include/swi.h.
 EXPORTS = ("swi_create", "swi_set_potential", "swi_set_absorber", "swi_set_windows", "swi_plan_windows",
-           "swi_apply", "swi_apply_c64", "swi_solve", "swi_get_window_info", "swi_get_eigenpairs", "swi_copy_eigenpairs",
+           "swi_apply", "swi_apply_ds", "swi_apply_c64", "swi_solve", "swi_get_window_info", "swi_get_eigenpairs", "swi_copy_eigenpairs",
            "swi_set_eigenpairs", "swi_residuals", "swi_transmission", "swi_grad", "swi_profile",
            "swi_profile_read", "swi_transmission_noalloc", "swi_last_error", "swi_launch_count", "swi_destroy")
 
@@ -77,6 +77,7 @@ def load(path: str = LIB_PATH):
         "swi_set_windows": (I, [VP, I, VP, VP]),
         "swi_plan_windows": (I, [VP, I, I, D, D, D, VP, VP]),
         "swi_apply": (I, [VP, I, VP, VP, VP, I]),
+        "swi_apply_ds": (I, [VP, I, VP, VP, VP, I]),
         "swi_apply_c64": (I, [VP, I, VP, VP, VP, I]),
         "swi_solve": (I, [VP, P(SolveOpts), P(SolveInfo)]),
         "swi_get_window_info": (I, [VP, I, P(WindowInfo), P(I)]),
@@ -204,6 +205,19 @@ class Context:
         X = _c_arr(X, np.complex128)
         Y = np.empty_like(X)
         self._check(self._lib.swi_apply(self._h, X.shape[1], _ptr(sig), _ptr(X), _ptr(Y), 0))
+        return Y
+
+    def apply_ds(self, X, sigma):
+        """apply() in double-single arithmetic (the operator of the double-single Krylov loop)."""
+        sig = _c_arr(np.broadcast_to(np.asarray(sigma, dtype=np.float64), (X.shape[1],)), np.float64)
+        if _is_device(X):
+            import torch
+            Y = torch.empty_like(X)
+            self._check(self._lib.swi_apply_ds(self._h, X.shape[1], _ptr(sig), _ptr(X), _ptr(Y), 1))
+            return Y
+        X = _c_arr(X, np.complex128)
+        Y = np.empty_like(X)
+        self._check(self._lib.swi_apply_ds(self._h, X.shape[1], _ptr(sig), _ptr(X), _ptr(Y), 0))
         return Y
 
     def apply_c64(self, X, sigma):

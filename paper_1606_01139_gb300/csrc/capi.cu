@@ -225,13 +225,16 @@ void copy_in(DevMem& dst, const void* src, size_t bytes, bool on_device, cudaStr
 void sync(cudaStream_t s) { SWI_CUDA_TRY(cudaStreamSynchronize(s)); }
 
 // Y[:, c] = (A - sigma_c) X[:, c] in chunks of columns, sigma from the context's sigma table
-void apply_block(swi_ctx* c, const double2* X, int ldx, double2* Y, int ldy, int ncols) {
+void apply_block(swi_ctx* c, const double2* X, int ldx, double2* Y, int ldy, int ncols, bool ds = false) {
   const swi::StencilParams P = stencil_params(c);
   for (int c0 = 0; c0 < ncols; c0 += 32) {
     swi::StencilBatch bt;
     bt.n = 1;
     bt.blk[0] = swi::StencilBlock{X + c0, Y + c0, ldx, ldy, std::min(32, ncols - c0), c0};
-    swi::launch_stencil(P, bt, c->sig_dev.as<double>(), c->stream, &c->launches);
+    if (ds)
+      swi::launch_stencil_ds(P, bt, c->sig_dev.as<double>(), c->stream, &c->launches);
+    else
+      swi::launch_stencil(P, bt, c->sig_dev.as<double>(), c->stream, &c->launches);
   }
 }
 
@@ -552,7 +555,10 @@ swi_status do_solve(swi_ctx* c, const swi_solve_opts* o, swi_solve_info* info) {
       }
       const double Nn = (double)c->N;
       ProfScope ps(c, SWI_K_STENCIL, kStencilFlops * Nn * b * na, (32.0 * b + 16.0) * Nn * na);
-      swi::launch_stencil(P, sb, c->sig_dev.as<double>(), c->stream, &c->launches);
+      if (c->arith == SWI_ARITH_F64)
+        swi::launch_stencil(P, sb, c->sig_dev.as<double>(), c->stream, &c->launches);
+      else
+        swi::launch_stencil_ds(P, sb, c->sig_dev.as<double>(), c->stream, &c->launches);
     }
     // 2) block classical Gram-Schmidt, twice, against [Q_j V_j]
     for (int pass = 0; pass < 2; ++pass) {
@@ -938,7 +944,7 @@ swi_status swi_plan_windows(swi_ctx* c, int n_r, int p, double e_min, double e_m
   });
 }
 
-swi_status swi_apply(swi_ctx* c, int nvec, const double* sigma, const void* X, void* Y, int on_device) {
+swi_status apply_impl(swi_ctx* c, int nvec, const double* sigma, const void* X, void* Y, int on_device, bool ds) {
   return guarded(c, [&]() -> swi_status {
     if (nvec < 1 || !sigma || !X || !Y) return fail(c, SWI_EINVAL, "bad arguments");
     if (!c->has_V || !c->has_G) return fail(c, SWI_ESTATE, "potential and absorbers must be set");
@@ -946,7 +952,7 @@ swi_status swi_apply(swi_ctx* c, int nvec, const double* sigma, const void* X, v
     c->sig_dev.ensure(sizeof(double) * std::max(nvec, 64));
     SWI_CUDA_TRY(cudaMemcpyAsync(c->sig_dev.p, sigma, sizeof(double) * nvec, cudaMemcpyHostToDevice, c->stream));
     if (on_device) {
-      apply_block(c, static_cast<const double2*>(X), nvec, static_cast<double2*>(Y), nvec, nvec);
+      apply_block(c, static_cast<const double2*>(X), nvec, static_cast<double2*>(Y), nvec, nvec, ds);
       sync(c->stream);
       return SWI_OK;
     }
@@ -954,11 +960,19 @@ swi_status swi_apply(swi_ctx* c, int nvec, const double* sigma, const void* X, v
     dx.ensure(bytes);
     dy.ensure(bytes);
     SWI_CUDA_TRY(cudaMemcpyAsync(dx.p, X, bytes, cudaMemcpyHostToDevice, c->stream));
-    apply_block(c, dx.as<double2>(), nvec, dy.as<double2>(), nvec, nvec);
+    apply_block(c, dx.as<double2>(), nvec, dy.as<double2>(), nvec, nvec, ds);
     SWI_CUDA_TRY(cudaMemcpyAsync(Y, dy.p, bytes, cudaMemcpyDeviceToHost, c->stream));
     sync(c->stream);
     return SWI_OK;
   });
+}
+
+swi_status swi_apply(swi_ctx* c, int nvec, const double* sigma, const void* X, void* Y, int on_device) {
+  return apply_impl(c, nvec, sigma, X, Y, on_device, false);
+}
+
+swi_status swi_apply_ds(swi_ctx* c, int nvec, const double* sigma, const void* X, void* Y, int on_device) {
+  return apply_impl(c, nvec, sigma, X, Y, on_device, true);
 }
 
 swi_status swi_apply_c64(swi_ctx* c, int nvec, const float* sigma, const void* X, void* Y, int on_device) {

@@ -24,6 +24,43 @@ __device__ __forceinline__ df from_d(double x) {
 }
 __device__ __forceinline__ double to_d(df a) { return (double)a.h + (double)a.l; }
 
+// x = hi + lo from the bit fields of x, on the integer and FP32 pipes (GB300's
+// FP64 pipe is the scarce one): hi is x rounded to 24 significant bits, lo the
+// signed 29-bit remainder rounded to a float, so |x - hi - lo| <= 2^-48 |x| as
+// with an FP64 split.  Magnitudes below 2^-74 (where the remainder would leave
+// the float range) and near the top of the float range take the FP64 route.
+__device__ __forceinline__ void split_bits(double x, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned int top = (unsigned int)(b >> 32);
+  const unsigned int sgn = top & 0x80000000u;
+  const int e = (int)((top >> 20) & 0x7ff);
+  if (e >= 949 && e <= 1149) {
+    const unsigned int up = (unsigned int)(b >> 28) & 1u;  // round half up on the first dropped bit
+    const unsigned int fb = ((unsigned int)(e - 896) << 23 | ((unsigned int)(b >> 29) & 0x7fffffu)) + up;
+    hi = __uint_as_float(sgn | fb);
+    const int rem = (int)((unsigned int)b & 0x1fffffffu) - (int)(up << 29);  // x - hi in units of 2^(e-1075)
+    const float t = (float)rem * __uint_as_float((unsigned int)(e - 948) << 23);
+    lo = sgn ? -t : t;
+  } else {
+    hi = __double2float_rn(x);
+    lo = __double2float_rn(x - (double)hi);
+  }
+}
+
+// (s, e) += a * b with a, b double-single: the product is formed exactly up to
+// its tail with FMA, the head added with TwoSum (Knuth), errors kept in e.
+__device__ __forceinline__ void fma_acc(float& s, float& e, float ah, float al, float bh, float bl) {
+  const float p = ah * bh;
+  float pe = fmaf(ah, bh, -p);
+  pe = fmaf(ah, bl, pe);
+  pe = fmaf(al, bh, pe);
+  const float t = s + p;
+  const float bp = t - s;
+  const float err = (s - (t - bp)) + (p - bp);
+  s = t;
+  e += err + pe;
+}
+
 __device__ __forceinline__ df quick_two_sum(float a, float b) {
   const float s = a + b;
   return df{s, b - (s - a)};

@@ -113,6 +113,9 @@ struct StencilBatch {
 
 void launch_stencil(const StencilParams& P, const StencilBatch& batch, const double* sigma_dev,
                     cudaStream_t s, long long* launches);
+// The same batched operator in double-single arithmetic (complex128 in and out).
+void launch_stencil_ds(const StencilParams& P, const StencilBatch& batch, const double* sigma_dev, cudaStream_t s,
+                       long long* launches);
 
 // ---------------------------------------------------------------- tall-skinny products
 // C_j = op(X_j)^H diag(w) Y_j over the N rows (op = conj for the Hermitian

@@ -90,6 +90,38 @@ def test_stencil_device_pointers(swi):
     assert np.array_equal(Yd.cpu().numpy(), Yh)
 
 
+# double-single stencil: each of ~40 terms carries ~2^-47 of its magnitude,
+# and the terms sum to at most ||A||_G max|x| (Gershgorin).
+DS_STENCIL_TOL = 40 * 2.0 ** -47
+
+
+@pytest.mark.parametrize("shape", [(13, 9, 17), (6, 20, 7), (33, 17, 40)])
+@pytest.mark.parametrize("bc", [0, 1])
+def test_stencil_ds_ragged(swi, shape, bc):
+    w = W.make_wire(*shape, 0.5, 4, 3)
+    rng = np.random.default_rng(21)
+    nvec = 7
+    X = rng.standard_normal((w.N, nvec)) + 1j * rng.standard_normal((w.N, nvec))
+    sig = rng.uniform(-2, 2, nvec)
+    with _ctx(swi, w, bc) as c:
+        Y = c.apply_ds(X, sig)
+    Yo = stencil.apply_A(X, w.nx, w.ny, w.nz, w.h, w.V, w.gamma_L, w.gamma_R, bc=bc) - X * sig[None, :]
+    an = stencil.gershgorin_norm(w.h, w.V, w.gamma_L, w.gamma_R)
+    assert np.max(np.abs(Y - Yo)) <= DS_STENCIL_TOL * (an + 2.0) * np.max(np.abs(X))
+
+
+def test_stencil_ds_full_size_block16(swi):
+    w = W.config_wire("wire_48x48x96")
+    rng = np.random.default_rng(22)
+    X = rng.standard_normal((w.N, 16)) + 1j * rng.standard_normal((w.N, 16))
+    sig = np.linspace(-1.0, 0.5, 16)
+    with _ctx(swi, w) as c:
+        Y = c.apply_ds(X, sig)
+    Yo = stencil.apply_A(X, w.nx, w.ny, w.nz, w.h, w.V, w.gamma_L, w.gamma_R) - X * sig[None, :]
+    an = stencil.gershgorin_norm(w.h, w.V, w.gamma_L, w.gamma_R)
+    assert np.max(np.abs(Y - Yo)) <= DS_STENCIL_TOL * (an + 2.0) * np.max(np.abs(X))
+
+
 # complex64 stencil: FP32 rounding of ~40 terms whose magnitudes sum to at most
 # ||A||_G max|x| (Gershgorin), plus the FP32 copies of V, Gamma, sigma and the
 # weights: |Y - Y_FP64| <= 40 * 2^-24 * ||A||_G max|X| ~ 2.4e-6 ||A||_G max|X|.

@@ -304,8 +304,10 @@ __global__ void __launch_bounds__(256, 2) gram_oz_kernel(const __grid_constant__
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wm = warp & 3, wn = warp >> 2;
   const int g = lane >> 2, t = lane & 3;
-  // loader roles: X column li (of the tile), rows 2 lr, 2 lr + 1 (+8 k); Y column yj, rows 2 yr, 2 yr + 1
-  const int li = tid % kTI, lr = tid / kTI;   // lr in 0..3
+  // loader roles: X column li (of the tile), rows 2 lr, 2 lr + 1 (+8 k); Y column yj, rows 2 yr, 2 yr + 1.
+  // The four lanes of one column are adjacent: their digit-plane stores fall in
+  // distinct banks, and the column's exponent is combined by shuffles.
+  const int li = tid >> 2, lr = tid & 3;
   const int yj = tid % kTJ, yr = tid / kTJ;   // yr in 0..15
   float ohi[2][4], olo[2][4];  // double-single running sums (re, im) of the warp's C fragment
 #pragma unroll
@@ -346,10 +348,11 @@ __global__ void __launch_bounds__(256, 2) gram_oz_kernel(const __grid_constant__
       for (int h = 0; h < 2; ++h) ex_loc = max(ex_loc, max(efield(xv[k][h].x), efield(xv[k][h].y)));
 #pragma unroll
     for (int h = 0; h < 2; ++h) ey_loc = max(ey_loc, max(efield(yv[h].x), efield(yv[h].y)));
-    if (tid < kTI) emx[tid] = 0;
+    ex_loc = max(ex_loc, __shfl_xor_sync(0xffffffffu, ex_loc, 1));
+    ex_loc = max(ex_loc, __shfl_xor_sync(0xffffffffu, ex_loc, 2));
     if (tid < kTJ) emy[tid] = 0;
     __syncthreads();
-    atomicMax(&emx[li], ex_loc);
+    if (lr == 0) emx[li] = ex_loc;
     atomicMax(&emy[yj], ey_loc);
     __syncthreads();
     // 2) digit planes: A = conj(X)^T rows li, Y columns yj; rows paired in one 32-bit word

@@ -221,6 +221,27 @@ def test_wire_10x10x20_double_single(swi):
     _check_pairs(w, eps_o, U_o, eps, U, res, info, 48, RES_TOL_DS)
 
 
+@pytest.mark.parametrize("name,shape", [("wire_48x48x96", (10, 10, 24)), ("wire_96x96x192", (10, 10, 24)),
+                                        ("wire_64x64x128", (10, 10, 20))])
+def test_reduced_copies(swi, name, shape):
+    # small copies of the larger workloads (same recipe and seed): 32 pairs in
+    # 4 windows in double-single arithmetic against the dense spectrum, then
+    # T(E) and the adjoint against the oracle on the same pairs
+    w = W.reduced_wire(name, *shape)
+    A, eps_o, U_o, eps, U, res, info, winfo = _solve_vs_dense(swi, w, 32, 4, block=8, arith=swi.ARITH_DS)
+    _check_pairs(w, eps_o, U_o, eps, U, res, info, 32, RES_TOL_DS)
+    E = W.energy_grid(eps.real[0], eps.real[-1], 16)
+    To = transport.transmission_spectral(eps, U, w.gamma_L, w.gamma_R, E)
+    wts = np.random.default_rng(9).standard_normal(len(E))
+    dVo = transport.grad_V_spectral(eps, U, w.gamma_L, w.gamma_R, E, wts)
+    with _ctx(swi, w) as c:
+        c.set_eigenpairs(eps, U)
+        T = c.transmission(E)
+        dV, dE = c.grad(E, wts)
+    assert np.max(np.abs(T - To)) <= 1e-9 * max(1.0, np.max(np.abs(To)))
+    assert np.max(np.abs(dV - dVo)) <= 1e-9 * max(1.0, np.max(np.abs(dVo)))
+
+
 @pytest.fixture(scope="module")
 def wire10(swi):
     w = W.config_wire("wire_10x10x20")

@@ -153,6 +153,14 @@ def config_wire(name: str) -> Wire:
     return make_wire(c["nx"], c["ny"], c["nz"], c["h"], c["n_wells"], c["seed"])
 
 
+def reduced_wire(name: str, nx: int = 10, ny: int = 10, nz: int = 24) -> Wire:
+    """A small copy of a workload for dense-oracle parity: same h, seed and recipe,
+    wells scaled with the wire length (n_wells * nz / nz_full, at least 2)."""
+    c = CONFIGS[name]
+    wells = max(2, int(round(c["n_wells"] * nz / c["nz"])))
+    return make_wire(nx, ny, nz, c["h"], wells, c["seed"])
+
+
 def batch_systems(seed: int = 4, count: int = 64):
     """The uneven batch: per system (nx, ny, nz, n_wells, n_pairs, p, sub_seed)."""
     rng = np.random.default_rng(seed)

@@ -239,6 +239,18 @@ def stencil_c64_rate(swi, stream, hbm, launches=20, warm=3):
                     "FP64 step; inputs larger than L2"}
 
 
+def aggregate(elapsed, units, dist=None, device="cpu"):
+    """Whole-job figures over the ranks of a replica run: the slowest rank's time
+    and the units (converged pairs) of all ranks."""
+    import torch
+    t = torch.tensor([float(elapsed)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -367,12 +379,7 @@ def main():
     launches = ctx.launch_count() - launches0
     units = sum(i["n_converged"] for i in infos)
 
-    t = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
-    u = torch.tensor([float(units)], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-    elapsed_max, units_all = float(t.item()), float(u.item())
+    elapsed_max, units_all = aggregate(elapsed, units, dist, "cuda")
 
     if rank != 0:
         if dist is not None:

@@ -222,7 +222,7 @@ __device__ __forceinline__ void mma_flush(const unsigned* adig, const unsigned* 
       for (int c = 0; c < 2; ++c)
 #pragma unroll
         for (int e = 0; e < 4; ++e) acc[d][c][e] = 0.f;
-#pragma unroll
+#pragma unroll 1  // unrolled, the fragment loads of both k steps stay live and spill at 128 registers
     for (int ks = 0; ks < kKC / 16; ++ks) {
       const int kw = ks * 8 + t;  // word of k = 16 ks + 2 t
       unsigned bre[kDig][2], bim[kDig][2];

@@ -207,6 +207,51 @@ swi_status swi_set_eigenpairs(swi_ctx* ctx, int n, const void* eps, const void* 
  * current pairs (host array of n doubles). */
 swi_status swi_residuals(swi_ctx* ctx, double* res_out);
 
+/* Options of swi_refine (zero-initialise; zero fields take the defaults). */
+typedef struct {
+  int max_sweeps;       /* sweeps at most (default 3) */
+  int group;            /* consecutive pairs (by real part) per Rayleigh-Ritz
+                           problem, n_g (default 16; 1..32) */
+  int arith;            /* as swi_solve_opts.arith (products and the projected
+                           Schur step; stencil and residuals are native FP64) */
+  int reserved;
+  double rel_tol;       /* target relative residual, as in swi_solve (default 1e-10) */
+  double eq_rtol;       /* Algorithm 2 tests applied to the refined pairs, as */
+  double drop_tol;      /* in swi_solve_opts (defaults 1e-8, 1e-6) */
+} swi_refine_opts;
+
+typedef struct {
+  int sweeps;           /* sweeps carried out */
+  int n_pairs;          /* pairs after the last sweep */
+  int n_converged;      /* of those, pairs with relative residual <= rel_tol */
+  int n_dropped;        /* pairs removed as redundant by Algorithm 2 */
+  long long matvecs;    /* operator applications (vectors) */
+  double max_rel_res_in;   /* largest relative residual before the first sweep */
+  double max_rel_res;      /* ... and after the last one */
+  double t_s;           /* wall time */
+} swi_refine_info;
+
+/* FP64 residual-correction sweeps on the current pairs (from swi_solve or
+ * swi_set_eigenpairs): the Rayleigh-Ritz refinement of Section 1 applied to
+ * the pairs themselves.  Pairs, ordered by real part, are cut into groups of
+ * n_g; a group holding a pair with relative residual above rel_tol is
+ * replaced by the Rayleigh-Ritz pairs of span[U_g, R_u], R_u = A U_u -
+ * U_u diag(eps_u) over its unconverged pairs u: with Q an orthonormal basis
+ * of that span (block Gram-Schmidt twice, Cholesky-QR2) and sigma_g the
+ * middle of the group's real parts, the n_g eigenvalues theta of the pencil
+ * Q^T (A - sigma_g) Q y = theta Q^T Q y (the unconjugated form, under which
+ * the eigenvectors of the complex-symmetric A are bi-orthogonal, Section 1)
+ * of smallest magnitude (the windows' SM selection, Eq. 3) give
+ * eps = sigma_g + theta and U = Q y.  All pairs then pass Algorithm 2 as
+ * one window (equal-eigenvalue projection, redundancy drop, U^T U = I), and
+ * the explicit FP64 residuals are recomputed; sweeps stop when every pair is
+ * at rel_tol.  The pairs stay in library-owned memory (swi_get_eigenpairs).
+ * Errors: SWI_ESTATE (no pairs, or no potential/absorbers), SWI_EINVAL,
+ * SWI_ENOCONV (pairs above rel_tol after max_sweeps, the refined pairs are
+ * kept; or a singular Q^T Q / an unconverged projected problem, the pairs of
+ * the previous sweep are kept), SWI_ENOMEM, SWI_ECUDA. */
+swi_status swi_refine(swi_ctx* ctx, const swi_refine_opts* opts, swi_refine_info* info);
+
 /* T(E_e) = Tr{G Gamma_R G^dagger Gamma_L} (Section 1) for nE energies through
  * the spectral G of the current pairs:  R = U^T Gamma_R conj(U),
  * L = U^T Gamma_L conj(U), W = R o L, T_e = sum_kl g_ek W_kl conj(g_el),

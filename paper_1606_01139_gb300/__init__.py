@@ -26,7 +26,7 @@ ARITH_DS, ARITH_F64 = 2, 1
 
 # Every entry point declared in include/swi.h.
 EXPORTS = ("swi_create", "swi_set_potential", "swi_set_absorber", "swi_set_windows", "swi_plan_windows",
-           "swi_apply", "swi_apply_ds", "swi_apply_c64", "swi_solve", "swi_get_window_info", "swi_get_eigenpairs", "swi_copy_eigenpairs",
+           "swi_apply", "swi_apply_ds", "swi_apply_c64", "swi_solve", "swi_refine", "swi_get_window_info", "swi_get_eigenpairs", "swi_copy_eigenpairs",
            "swi_set_eigenpairs", "swi_residuals", "swi_transmission", "swi_grad", "swi_profile",
            "swi_profile_read", "swi_transmission_noalloc", "swi_last_error", "swi_launch_count", "swi_destroy")
 
@@ -41,6 +41,20 @@ class SolveOpts(C.Structure):
     _fields_ = [("block", C.c_int), ("max_basis", C.c_int), ("keep", C.c_int), ("arith", C.c_int),
                 ("max_matvecs", C.c_longlong), ("rel_tol", C.c_double), ("eq_rtol", C.c_double),
                 ("drop_tol", C.c_double), ("seed", C.c_ulonglong), ("n_keep", C.c_int), ("reserved1", C.c_int)]
+
+
+class RefineOpts(C.Structure):
+    _fields_ = [("max_sweeps", C.c_int), ("group", C.c_int), ("arith", C.c_int), ("reserved", C.c_int),
+                ("rel_tol", C.c_double), ("eq_rtol", C.c_double), ("drop_tol", C.c_double)]
+
+
+class RefineInfo(C.Structure):
+    _fields_ = [("sweeps", C.c_int), ("n_pairs", C.c_int), ("n_converged", C.c_int), ("n_dropped", C.c_int),
+                ("matvecs", C.c_longlong), ("max_rel_res_in", C.c_double), ("max_rel_res", C.c_double),
+                ("t_s", C.c_double)]
+
+    def as_dict(self):
+        return {f[0]: getattr(self, f[0]) for f in self._fields_}
 
 
 class WindowInfo(C.Structure):
@@ -80,6 +94,7 @@ def load(path: str = LIB_PATH):
         "swi_apply_ds": (I, [VP, I, VP, VP, VP, I]),
         "swi_apply_c64": (I, [VP, I, VP, VP, VP, I]),
         "swi_solve": (I, [VP, P(SolveOpts), P(SolveInfo)]),
+        "swi_refine": (I, [VP, P(RefineOpts), P(RefineInfo)]),
         "swi_get_window_info": (I, [VP, I, P(WindowInfo), P(I)]),
         "swi_get_eigenpairs": (I, [VP, P(I), P(VP), P(VP), P(I)]),
         "swi_copy_eigenpairs": (I, [VP, VP, VP, I]),
@@ -277,6 +292,18 @@ class Context:
             return self._check(self._lib.swi_set_eigenpairs(self._h, U.shape[1], _ptr(eps), _ptr(U), 1))
         e, Uc = _c_arr(eps, np.complex128), _c_arr(U, np.complex128)
         return self._check(self._lib.swi_set_eigenpairs(self._h, Uc.shape[1], _ptr(e), _ptr(Uc), 0))
+
+    def refine(self, max_sweeps=3, group=16, rel_tol=1e-10, arith=ARITH_DS, eq_rtol=0.0, drop_tol=0.0,
+               allow=(SWI_OK, SWI_ENOCONV)):
+        """Residual-correction sweeps on the current pairs (Rayleigh-Ritz on span[U_g, R_u] per group of
+        `group` consecutive pairs, then Algorithm 2 as one window); returns the info dict with "status"."""
+        o = RefineOpts(max_sweeps=max_sweeps, group=group, arith=arith, rel_tol=rel_tol, eq_rtol=eq_rtol,
+                       drop_tol=drop_tol)
+        info = RefineInfo()
+        rc = self._check(self._lib.swi_refine(self._h, C.byref(o), C.byref(info)), allow)
+        d = info.as_dict()
+        d["status"] = STATUS_NAMES[rc]
+        return d
 
     def residuals(self):
         r = np.empty(self.n_pairs())

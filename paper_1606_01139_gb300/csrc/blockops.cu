@@ -245,7 +245,49 @@ __global__ void copy_block_kernel(const double2* __restrict__ src, int lds, doub
   dst[r * ldd + c] = src[r * lds + c];
 }
 
+// dst[:, q] = src[:, idx[q]], q < n
+__global__ void gather_cols_kernel(const double2* __restrict__ src, int lds, const int* __restrict__ idx, int n,
+                                   double2* __restrict__ dst, int ldd, int rows) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)rows * n) return;
+  const long long r = t / n;
+  const int q = (int)(t % n);
+  dst[r * ldd + q] = src[r * lds + idx[q]];
+}
+
+// Y[:, q] -= eps[q] X[:, q], q < n (complex eps)
+__global__ void sub_diag_kernel(double2* __restrict__ Y, int ldy, const double2* __restrict__ X, int ldx,
+                                const double2* __restrict__ eps, int n, int rows) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)rows * n) return;
+  const long long r = t / n;
+  const int q = (int)(t % n);
+  const double2 x = X[r * ldx + q], e = eps[q];
+  double2 y = Y[r * ldy + q];
+  y.x -= e.x * x.x - e.y * x.y;
+  y.y -= e.x * x.y + e.y * x.x;
+  Y[r * ldy + q] = y;
+}
+
 }  // namespace
+
+void launch_gather_cols(const double2* src, int lds, const int* idx, int n, double2* dst, int ldd, int rows,
+                        cudaStream_t s, long long* launches) {
+  const long long t = (long long)rows * n;
+  if (t == 0) return;
+  gather_cols_kernel<<<(unsigned)((t + 255) / 256), 256, 0, s>>>(src, lds, idx, n, dst, ldd, rows);
+  SWI_CHECK_LAUNCH();
+  if (launches) ++*launches;
+}
+
+void launch_sub_diag(double2* Y, int ldy, const double2* X, int ldx, const double2* eps, int n, int rows,
+                     cudaStream_t s, long long* launches) {
+  const long long t = (long long)rows * n;
+  if (t == 0) return;
+  sub_diag_kernel<<<(unsigned)((t + 255) / 256), 256, 0, s>>>(Y, ldy, X, ldx, eps, n, rows);
+  SWI_CHECK_LAUNCH();
+  if (launches) ++*launches;
+}
 
 void launch_gram(const GramBatch& b, int N, const double* w, int bilinear, double2* work, size_t work_elems,
                  cudaStream_t s, long long* launches) {

@@ -326,6 +326,78 @@ void cholqr2(swi_ctx* c, std::vector<Window*>& ws, const std::vector<int>& col, 
   }
 }
 
+// Algorithm 2 over n_all pairs of nwin windows (U [N][ldu] on the device, not
+// the context's own pair buffer; eps and window index on the host, windows in
+// shift order), selection of the n_keep lowest (0: all), U^T U = I; the
+// survivors become the context's pairs.  minfo: nout, n_dup, n_holes, status.
+void merge_pairs(swi_ctx* c, const double2* Uin, int ldu, const std::vector<double2>& eps_all,
+                 const std::vector<int>& win_of, int nwin, double eq_rtol, double drop_tol, int n_keep, int* minfo) {
+  const int n_all = (int)eps_all.size();
+  const int pair_cap = std::max(4 * n_all, 1024);
+  c->m_eps_all.ensure(sizeof(double2) * n_all);
+  c->m_win.ensure(sizeof(int) * n_all);
+  SWI_CUDA_TRY(cudaMemcpyAsync(c->m_eps_all.p, eps_all.data(), sizeof(double2) * n_all, cudaMemcpyHostToDevice,
+                               c->stream));
+  SWI_CUDA_TRY(cudaMemcpyAsync(c->m_win.p, win_of.data(), sizeof(int) * n_all, cudaMemcpyHostToDevice, c->stream));
+  c->m_comp.ensure(sizeof(int) * n_all);
+  c->m_pairs.ensure(sizeof(int) * 2 * pair_cap);
+  c->m_counts.ensure(sizeof(int) * 4);
+  c->m_work.ensure(sizeof(double2) * (size_t)pair_cap * 2 * 304);
+  c->m_gram.ensure(sizeof(double2) * 2 * pair_cap);
+  c->m_kept.ensure(sizeof(int) * n_all);
+  c->m_order.ensure(sizeof(int) * n_all);
+  c->m_holes.ensure(sizeof(int) * (nwin + 1));
+  c->m_src.ensure(sizeof(int) * swi::merge_src_elems(n_all));
+  c->m_coef.ensure(sizeof(double2) * swi::merge_coef_elems(n_all));
+  c->m_nterm.ensure(sizeof(int) * (n_all + 1));
+  c->m_info.ensure(sizeof(int) * 4);
+  c->m_eps_out.ensure(sizeof(double2) * n_all);
+  swi::MergeArgs ma;
+  ma.U = Uin;
+  ma.ldu = ldu;
+  ma.N = c->N;
+  ma.n = n_all;
+  ma.p = nwin;
+  ma.eps = c->m_eps_all.as<double2>();
+  ma.win = c->m_win.as<int>();
+  ma.eq_rtol = eq_rtol;
+  ma.drop_tol = drop_tol;
+  ma.n_keep = n_keep;
+  ma.comp = c->m_comp.as<int>();
+  ma.pairs = c->m_pairs.as<int>();
+  ma.pair_cap = pair_cap;
+  ma.counts = c->m_counts.as<int>();
+  ma.work = c->m_work.as<double2>();
+  ma.work_elems = c->m_work.bytes / sizeof(double2);
+  ma.gram = c->m_gram.as<double2>();
+  ma.kept = c->m_kept.as<int>();
+  ma.order = c->m_order.as<int>();
+  ma.holes = c->m_holes.as<int>();
+  ma.src = c->m_src.as<int>();
+  ma.coef = c->m_coef.as<double2>();
+  ma.nterm = c->m_nterm.as<int>();
+  ma.out_eps = c->m_eps_out.as<double2>();
+  ma.info = c->m_info.as<int>();
+  {
+    ProfScope ps(c, SWI_K_MERGE, 0.0, 16.0 * c->N * (double)n_all);
+    swi::merge_run(ma, c->stream, &c->launches);
+  }
+  SWI_CUDA_TRY(cudaMemcpyAsync(minfo, c->m_info.p, sizeof(int) * 4, cudaMemcpyDeviceToHost, c->stream));
+  sync(c->stream);
+  const int nout = minfo[0];
+  c->U.ensure(sizeof(double2) * (size_t)c->N * std::max(nout, 1));
+  c->eps.ensure(sizeof(double2) * std::max(nout, 1));
+  ma.out_U = c->U.as<double2>();
+  ma.ldo = nout;
+  {
+    ProfScope ps(c, SWI_K_MERGE, 0.0, 16.0 * c->N * (double)(n_all + nout));
+    swi::merge_apply(ma, nout, c->stream, &c->launches);
+  }
+  SWI_CUDA_TRY(cudaMemcpyAsync(c->eps.p, c->m_eps_out.p, sizeof(double2) * nout, cudaMemcpyDeviceToDevice, c->stream));
+  c->npairs = nout;
+  c->have_RL = false;
+}
+
 swi_status do_solve(swi_ctx* c, const swi_solve_opts* o, swi_solve_info* info) {
   if (!c->has_V || !c->has_G) return fail(c, SWI_ESTATE, "potential and absorbers must be set before solve");
   if (c->sigma.empty()) return fail(c, SWI_ESTATE, "windows must be set before solve");
@@ -665,70 +737,9 @@ swi_status do_solve(swi_ctx* c, const swi_solve_opts* o, swi_solve_info* info) {
   const double t1 = swi::now_seconds();
 
   // ---- Algorithm 2 merge, selection, U^T U = I
-  const int pair_cap = std::max(4 * n_all, 1024);
-  c->m_eps_all.ensure(sizeof(double2) * n_all);
-  c->m_win.ensure(sizeof(int) * n_all);
-  SWI_CUDA_TRY(cudaMemcpyAsync(c->m_eps_all.p, eps_all.data(), sizeof(double2) * n_all, cudaMemcpyHostToDevice,
-                               c->stream));
-  SWI_CUDA_TRY(cudaMemcpyAsync(c->m_win.p, win_of.data(), sizeof(int) * n_all, cudaMemcpyHostToDevice, c->stream));
-  c->m_comp.ensure(sizeof(int) * n_all);
-  c->m_pairs.ensure(sizeof(int) * 2 * pair_cap);
-  c->m_counts.ensure(sizeof(int) * 4);
-  c->m_work.ensure(sizeof(double2) * (size_t)pair_cap * 2 * 304);
-  c->m_gram.ensure(sizeof(double2) * 2 * pair_cap);
-  c->m_kept.ensure(sizeof(int) * n_all);
-  c->m_order.ensure(sizeof(int) * n_all);
-  c->m_holes.ensure(sizeof(int) * (nwin + 1));
-  c->m_src.ensure(sizeof(int) * swi::merge_src_elems(n_all));
-  c->m_coef.ensure(sizeof(double2) * swi::merge_coef_elems(n_all));
-  c->m_nterm.ensure(sizeof(int) * (n_all + 1));
-  c->m_info.ensure(sizeof(int) * 4);
-  c->m_eps_out.ensure(sizeof(double2) * n_all);
-  swi::MergeArgs ma;
-  ma.U = c->Uall.as<double2>();
-  ma.ldu = n_all;
-  ma.N = c->N;
-  ma.n = n_all;
-  ma.p = nwin;
-  ma.eps = c->m_eps_all.as<double2>();
-  ma.win = c->m_win.as<int>();
-  ma.eq_rtol = eq_rtol;
-  ma.drop_tol = drop_tol;
-  ma.n_keep = opt.n_keep;
-  ma.comp = c->m_comp.as<int>();
-  ma.pairs = c->m_pairs.as<int>();
-  ma.pair_cap = pair_cap;
-  ma.counts = c->m_counts.as<int>();
-  ma.work = c->m_work.as<double2>();
-  ma.work_elems = c->m_work.bytes / sizeof(double2);
-  ma.gram = c->m_gram.as<double2>();
-  ma.kept = c->m_kept.as<int>();
-  ma.order = c->m_order.as<int>();
-  ma.holes = c->m_holes.as<int>();
-  ma.src = c->m_src.as<int>();
-  ma.coef = c->m_coef.as<double2>();
-  ma.nterm = c->m_nterm.as<int>();
-  ma.out_eps = c->m_eps_out.as<double2>();
-  ma.info = c->m_info.as<int>();
-  {
-    ProfScope ps(c, SWI_K_MERGE, 0.0, 16.0 * c->N * (double)n_all);
-    swi::merge_run(ma, c->stream, &c->launches);
-  }
   int minfo[4];
-  SWI_CUDA_TRY(cudaMemcpyAsync(minfo, c->m_info.p, sizeof(int) * 4, cudaMemcpyDeviceToHost, c->stream));
-  sync(c->stream);
+  merge_pairs(c, c->Uall.as<double2>(), n_all, eps_all, win_of, nwin, eq_rtol, drop_tol, opt.n_keep, minfo);
   const int nout = minfo[0];
-  c->U.ensure(sizeof(double2) * (size_t)c->N * std::max(nout, 1));
-  c->eps.ensure(sizeof(double2) * std::max(nout, 1));
-  ma.out_U = c->U.as<double2>();
-  ma.ldo = nout;
-  {
-    ProfScope ps(c, SWI_K_MERGE, 0.0, 16.0 * c->N * (double)(n_all + nout));
-    swi::merge_apply(ma, nout, c->stream, &c->launches);
-  }
-  SWI_CUDA_TRY(cudaMemcpyAsync(c->eps.p, c->m_eps_out.p, sizeof(double2) * nout, cudaMemcpyDeviceToDevice, c->stream));
-  c->npairs = nout;
-  c->have_RL = false;
   c->Uall.release();
   // explicit FP64 residuals of the delivered pairs
   {
@@ -760,6 +771,224 @@ swi_status do_solve(swi_ctx* c, const swi_solve_opts* o, swi_solve_info* info) {
   if (minfo[3] != 0) return fail(c, SWI_EINVAL, "merge: equal-eigenvalue component too large");
   if (any_noconv) return fail(c, SWI_ENOCONV, "some window did not converge within its matvec budget");
   if (minfo[2] > 0) return fail(c, SWI_HOLES, std::to_string(minfo[2]) + " interface(s) without redundancy");
+  return SWI_OK;
+}
+
+// Residual-correction sweeps (Rayleigh-Ritz on span[U_g, R_u] per group of
+// consecutive pairs, in the unconjugated form under which the eigenvectors of
+// the complex-symmetric A are bi-orthogonal, then Algorithm 2 over all pairs as
+// one window); see swi_refine in swi.h.
+swi_status do_refine(swi_ctx* c, const swi_refine_opts* o, swi_refine_info* info) {
+  if (c->npairs <= 0) return fail(c, SWI_ESTATE, "no eigenpairs");
+  if (!c->has_V || !c->has_G) return fail(c, SWI_ESTATE, "potential and absorbers must be set");
+  swi_refine_opts opt;
+  std::memset(&opt, 0, sizeof(opt));
+  if (o) opt = *o;
+  const int max_sweeps = opt.max_sweeps > 0 ? opt.max_sweeps : 3;
+  const int g = opt.group > 0 ? opt.group : 16;
+  if (g > 32) return fail(c, SWI_EINVAL, "group must be <= 32");
+  if (opt.arith != 0 && opt.arith != SWI_ARITH_DS && opt.arith != SWI_ARITH_F64)
+    return fail(c, SWI_EINVAL, "unknown arithmetic");
+  if (opt.rel_tol < 0 || opt.eq_rtol < 0 || opt.drop_tol < 0) return fail(c, SWI_EINVAL, "negative tolerance");
+  const double rel_tol = opt.rel_tol > 0 ? opt.rel_tol : 1e-10;
+  const double eq_rtol = opt.eq_rtol > 0 ? opt.eq_rtol : 1e-8;
+  const double drop_tol = opt.drop_tol > 0 ? opt.drop_tol : 1e-6;
+  c->arith = opt.arith == SWI_ARITH_F64 ? SWI_ARITH_F64 : SWI_ARITH_DS;
+  const double t0 = swi::now_seconds();
+  const size_t N = c->N;
+  if ((size_t)2 * g > N) return fail(c, SWI_EINVAL, "group larger than half the problem dimension");
+
+  // one group's workspace, reused group after group on the context's stream
+  Window w;
+  const int ld = 2 * g;
+  w.ld = ld;
+  w.Q[0].ensure(sizeof(double2) * N * ld);
+  w.W.ensure(sizeof(double2) * N * g);
+  w.C1.ensure(sizeof(double2) * ld * g);
+  w.C2.ensure(sizeof(double2) * ld * g);
+  w.G.ensure(sizeof(double2) * g * g);
+  w.R1.ensure(sizeof(double2) * g * g);
+  w.R1i.ensure(sizeof(double2) * g * g);
+  w.R2.ensure(sizeof(double2) * g * g);
+  w.R2i.ensure(sizeof(double2) * g * g);
+  w.H.ensure(sizeof(double2) * ld * ld);
+  w.Z.ensure(sizeof(double2) * ld * ld);
+  w.S.ensure(sizeof(double2) * ld * ld);
+  w.Bm.ensure(sizeof(double2) * ld);
+  w.Bz.ensure(sizeof(double2) * ld);
+  w.theta.ensure(sizeof(double2) * ld);
+  w.resid.ensure(sizeof(double) * ld);
+  w.Yw.ensure(sizeof(double2) * ld * g);
+  w.eps_w.ensure(sizeof(double2) * g);
+  w.res_w.ensure(sizeof(double) * g);
+  if (c->arith != SWI_ARITH_F64) {
+    w.Hw.ensure(16 * (size_t)ld * ld);
+    w.Zw.ensure(16 * (size_t)ld * ld);
+  }
+  SWI_CUDA_TRY(cudaMemsetAsync(w.Bm.p, 0, sizeof(double2) * ld, c->stream));  // no residual coupling
+  DevMem Xu, AQ, Sb, Unew, epsnew, eu, idx_dev, oinfo, sstat;
+  Sb.ensure(sizeof(double2) * ld * ld);
+  Xu.ensure(sizeof(double2) * N * g);
+  AQ.ensure(sizeof(double2) * N * ld);
+  gram_work_ensure(c, (size_t)4 << 20);
+  c->sig_dev.ensure(sizeof(double) * std::max(ld, 64));
+
+  long long mv = 0;
+  int n_dropped = 0, sweeps = 0;
+  if (c->resid.size() != (size_t)c->npairs) {
+    explicit_residuals(c, c->U.as<double2>(), c->npairs, c->eps.as<double2>(), c->npairs, c->resid);
+    mv += c->npairs;
+  }
+  double max_in = 0.0;
+  for (double r : c->resid) max_in = std::max(max_in, r);
+  auto all_converged = [&]() {
+    for (double r : c->resid)
+      if (!(r <= rel_tol)) return false;
+    return true;
+  };
+  while (sweeps < max_sweeps && !all_converged()) {
+    const int n = c->npairs;
+    const int ngroups = (n + g - 1) / g;
+    std::vector<double2> eh(n);
+    SWI_CUDA_TRY(cudaMemcpyAsync(eh.data(), c->eps.p, sizeof(double2) * n, cudaMemcpyDeviceToHost, c->stream));
+    sync(c->stream);
+    // unconverged pairs of every group, uploaded once
+    std::vector<int> idx, ioff(ngroups + 1, 0);
+    for (int gi = 0; gi < ngroups; ++gi) {
+      for (int k = gi * g; k < std::min(n, gi * g + g); ++k)
+        if (!(c->resid[k] <= rel_tol)) idx.push_back(k);
+      ioff[gi + 1] = (int)idx.size();
+    }
+    idx_dev.ensure(sizeof(int) * std::max<size_t>(idx.size(), 1));
+    SWI_CUDA_TRY(cudaMemcpyAsync(idx_dev.p, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice, c->stream));
+    Unew.ensure(sizeof(double2) * N * n);
+    epsnew.ensure(sizeof(double2) * n);
+    eu.ensure(sizeof(double2) * g);
+    oinfo.ensure(sizeof(int) * 4 * ngroups);
+    SWI_CUDA_TRY(cudaMemsetAsync(oinfo.p, 0, sizeof(int) * 4 * ngroups, c->stream));
+    sstat.ensure(sizeof(int) * ngroups);
+    SWI_CUDA_TRY(cudaMemsetAsync(sstat.p, 0, sizeof(int) * ngroups, c->stream));
+    std::vector<Window*> ws{&w};
+    for (int gi = 0; gi < ngroups; ++gi) {
+      const int lo = gi * g, ng = std::min(g, n - lo), nu = ioff[gi + 1] - ioff[gi];
+      double2* Ug = c->U.as<double2>() + lo;
+      if (nu == 0) {  // converged group: kept as it is
+        swi::launch_copy_block(Ug, n, Unew.as<double2>() + lo, n, c->N, ng, c->stream, &c->launches);
+        SWI_CUDA_TRY(cudaMemcpyAsync(epsnew.as<double2>() + lo, c->eps.as<double2>() + lo, sizeof(double2) * ng,
+                                     cudaMemcpyDeviceToDevice, c->stream));
+        continue;
+      }
+      const int m = ng + nu;
+      const int* ig = idx_dev.as<int>() + ioff[gi];
+      // Q[:, 0:ng] = orthonormal basis of U_g
+      swi::launch_copy_block(Ug, n, w.W.as<double2>(), ng, c->N, ng, c->stream, &c->launches);
+      cholqr2(c, ws, {0}, ng);
+      // R_u = A U_u - U_u diag(eps_u)
+      swi::launch_gather_cols(Ug - lo, n, ig, nu, Xu.as<double2>(), nu, c->N, c->stream, &c->launches);
+      swi::launch_gather_cols(c->eps.as<double2>(), 0, ig, nu, eu.as<double2>(), 0, 1, c->stream, &c->launches);
+      SWI_CUDA_TRY(cudaMemsetAsync(c->sig_dev.p, 0, sizeof(double) * nu, c->stream));
+      apply_block(c, Xu.as<double2>(), nu, w.W.as<double2>(), nu, nu);
+      swi::launch_sub_diag(w.W.as<double2>(), nu, Xu.as<double2>(), nu, eu.as<double2>(), nu, c->N, c->stream,
+                           &c->launches);
+      // block Gram-Schmidt twice against Q[:, 0:ng], then Cholesky-QR2 into Q[:, ng:m]
+      for (int pass = 0; pass < 2; ++pass) {
+        swi::GramBatch gb;
+        gb.n = 1;
+        gb.job[0] = swi::GramJob{w.Q[0].as<double2>(), w.W.as<double2>(), w.C1.as<double2>(), ld, nu, nu, ng, nu, 0};
+        gram_dispatch(c->arith, gb, c->N, nullptr, 0, c->gram_work.as<double2>(),
+                      c->gram_work.bytes / sizeof(double2), c->stream, &c->launches);
+        swi::RowGemmBatch rb;
+        rb.n = 1;
+        rb.job[0] = swi::RowGemmJob{w.Q[0].as<double2>(), w.C1.as<double2>(), w.W.as<double2>(), w.W.as<double2>(),
+                                    ld, nu, nu, nu, ng, nu, -1.0, 1.0};
+        rowgemm_dispatch(c->arith, rb, c->N, c->stream, &c->launches);
+      }
+      cholqr2(c, ws, {ng}, nu);
+      // (A - sigma_g) Q, sigma_g the middle of the group's real parts
+      double rmin = eh[lo].x, rmax = eh[lo].x;
+      for (int k = lo; k < lo + ng; ++k) {
+        rmin = std::min(rmin, eh[k].x);
+        rmax = std::max(rmax, eh[k].x);
+      }
+      const double sigma_g = 0.5 * (rmin + rmax);
+      {
+        std::vector<double> sg(m, sigma_g);
+        SWI_CUDA_TRY(cudaMemcpyAsync(c->sig_dev.p, sg.data(), sizeof(double) * m, cudaMemcpyHostToDevice, c->stream));
+        apply_block(c, w.Q[0].as<double2>(), ld, AQ.as<double2>(), ld, m);
+        sync(c->stream);  // sg leaves scope
+      }
+      {
+        // the pencil in the unconjugated form: K = Q^T (A - sigma_g) Q, S = Q^T Q, H = S^-1 K
+        swi::GramBatch gb;
+        gb.n = 1;
+        gb.job[0] = swi::GramJob{w.Q[0].as<double2>(), AQ.as<double2>(), w.H.as<double2>(), ld, ld, ld, m, m, 0};
+        gram_dispatch(c->arith, gb, c->N, nullptr, 1, c->gram_work.as<double2>(),
+                      c->gram_work.bytes / sizeof(double2), c->stream, &c->launches);
+        gb.job[0] = swi::GramJob{w.Q[0].as<double2>(), w.Q[0].as<double2>(), Sb.as<double2>(), ld, ld, ld, m, m, 0};
+        gram_dispatch(c->arith, gb, c->N, nullptr, 1, c->gram_work.as<double2>(),
+                      c->gram_work.bytes / sizeof(double2), c->stream, &c->launches);
+        swi::launch_small_solve(Sb.as<double2>(), w.H.as<double2>(), m, ld, sstat.as<int>() + gi, c->stream,
+                                &c->launches);
+      }
+      // Schur form, the ng Ritz values of smallest magnitude, their vectors
+      swi::SchurBatch sb;
+      sb.n = 1;
+      sb.job[0] = swi::SchurJob{w.H.as<double2>(), w.Z.as<double2>(), w.Bm.as<double2>(), w.Bz.as<double2>(),
+                                w.theta.as<double2>(), w.resid.as<double>(), w.S.as<double2>(),
+                                oinfo.as<int>() + 4 * gi, m, ld, 1, ng, ng, ng, 1.0, w.Hw.p, w.Zw.p};
+      if (c->arith == SWI_ARITH_F64) swi::launch_schur_batch(sb, c->stream, &c->launches);
+      else swi::launch_schur_ds_batch(sb, c->stream, &c->launches);
+      swi::RitzBatch fin;
+      fin.n = 1;
+      fin.job[0] = swi::RitzJob{w.Z.as<double2>(), w.S.as<double2>(), w.theta.as<double2>(), w.resid.as<double>(),
+                                oinfo.as<int>() + 4 * gi, w.Yw.as<double2>(), w.eps_w.as<double2>(),
+                                w.res_w.as<double>(), m, ld, ng, ng, sigma_g};
+      swi::launch_ritz_batch(fin, c->stream, &c->launches);
+      swi::RowGemmBatch rb;
+      rb.n = 1;
+      rb.job[0] = swi::RowGemmJob{w.Q[0].as<double2>(), w.Yw.as<double2>(), nullptr, Unew.as<double2>() + lo, ld, ng, 0,
+                                  n, m, ng, 1.0, 0.0};
+      rowgemm_dispatch(c->arith, rb, c->N, c->stream, &c->launches);
+      SWI_CUDA_TRY(cudaMemcpyAsync(epsnew.as<double2>() + lo, w.eps_w.p, sizeof(double2) * ng,
+                                   cudaMemcpyDeviceToDevice, c->stream));
+      mv += nu + m;
+    }
+    std::vector<int> oi(4 * ngroups), si(ngroups);
+    std::vector<double2> en(n);
+    SWI_CUDA_TRY(cudaMemcpyAsync(oi.data(), oinfo.p, sizeof(int) * 4 * ngroups, cudaMemcpyDeviceToHost, c->stream));
+    SWI_CUDA_TRY(cudaMemcpyAsync(si.data(), sstat.p, sizeof(int) * ngroups, cudaMemcpyDeviceToHost, c->stream));
+    SWI_CUDA_TRY(cudaMemcpyAsync(en.data(), epsnew.p, sizeof(double2) * n, cudaMemcpyDeviceToHost, c->stream));
+    sync(c->stream);
+    for (int gi = 0; gi < ngroups; ++gi) {
+      if (si[gi] != 0) return fail(c, SWI_ENOCONV, "refine: singular Q^T Q in a group");
+      if (oi[4 * gi + 2] != 0) return fail(c, SWI_ENOCONV, "refine: a projected eigenproblem did not converge");
+    }
+    // Algorithm 2 over the refined pairs as one window, U^T U = I
+    int minfo[4];
+    merge_pairs(c, Unew.as<double2>(), n, en, std::vector<int>(n, 0), 1, eq_rtol, drop_tol, 0, minfo);
+    if (minfo[3] != 0) return fail(c, SWI_EINVAL, "merge: equal-eigenvalue component too large");
+    n_dropped += minfo[1];
+    explicit_residuals(c, c->U.as<double2>(), c->npairs, c->eps.as<double2>(), c->npairs, c->resid);
+    mv += c->npairs;
+    ++sweeps;
+  }
+  int nconv = 0;
+  double maxr = 0.0;
+  for (double r : c->resid) {
+    if (r <= rel_tol) ++nconv;
+    maxr = std::max(maxr, r);
+  }
+  if (info) {
+    info->sweeps = sweeps;
+    info->n_pairs = c->npairs;
+    info->n_converged = nconv;
+    info->n_dropped = n_dropped;
+    info->matvecs = mv;
+    info->max_rel_res_in = max_in;
+    info->max_rel_res = maxr;
+    info->t_s = swi::now_seconds() - t0;
+  }
+  if (nconv < c->npairs) return fail(c, SWI_ENOCONV, "pairs above rel_tol after the last sweep");
   return SWI_OK;
 }
 
@@ -1011,6 +1240,10 @@ swi_status swi_apply_c64(swi_ctx* c, int nvec, const float* sigma, const void* X
 
 swi_status swi_solve(swi_ctx* c, const swi_solve_opts* opts, swi_solve_info* info) {
   return guarded(c, [&]() -> swi_status { return do_solve(c, opts, info); });
+}
+
+swi_status swi_refine(swi_ctx* c, const swi_refine_opts* opts, swi_refine_info* info) {
+  return guarded(c, [&]() -> swi_status { return do_refine(c, opts, info); });
 }
 
 swi_status swi_get_window_info(swi_ctx* c, int cap, swi_window_info* out, int* p) {

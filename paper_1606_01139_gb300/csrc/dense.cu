@@ -476,6 +476,64 @@ __global__ void ritz_kernel(const __grid_constant__ RitzBatch batch) {
   }
 }
 
+// H = S^-1 K for m x m complex matrices (row-major, leading dimension ld) by
+// Gauss-Jordan elimination with partial pivoting, one CTA; S is overwritten.
+// status: 0, or 1 + the column at which no nonzero pivot was left.
+__global__ void small_solve_kernel(double2* __restrict__ S, double2* __restrict__ H, int m, int ld, int* status) {
+  __shared__ double2 f[1024];
+  __shared__ int piv;
+  const int tid = threadIdx.x;
+  if (tid == 0) *status = 0;
+  for (int c = 0; c < m; ++c) {
+    if (tid == 0) {
+      int p = c;
+      double best = -1.0;
+      for (int r = c; r < m; ++r) {
+        const double a = cabs(S[(long long)r * ld + c]);
+        if (a > best) {
+          best = a;
+          p = r;
+        }
+      }
+      piv = best > 0.0 ? p : -1;
+      if (piv < 0) *status = 1 + c;
+    }
+    __syncthreads();
+    if (piv < 0) return;
+    if (piv != c) {  // swap rows c and piv of [S | H]
+      for (int j = tid; j < 2 * m; j += blockDim.x) {
+        double2* X = j < m ? S : H;
+        const int jj = j < m ? j : j - m;
+        const double2 t = X[(long long)c * ld + jj];
+        X[(long long)c * ld + jj] = X[(long long)piv * ld + jj];
+        X[(long long)piv * ld + jj] = t;
+      }
+    }
+    __syncthreads();
+    // scale row c by 1 / S[c][c]
+    const double2 inv = cdiv(make_double2(1.0, 0.0), S[(long long)c * ld + c]);
+    __syncthreads();
+    for (int j = tid; j < 2 * m; j += blockDim.x) {
+      double2* X = j < m ? S : H;
+      const int jj = j < m ? j : j - m;
+      X[(long long)c * ld + jj] = cmul(X[(long long)c * ld + jj], inv);
+    }
+    __syncthreads();
+    for (int r = tid; r < m; r += blockDim.x) f[r] = S[(long long)r * ld + c];
+    __syncthreads();
+    // eliminate column c from every other row
+    for (int e = tid; e < m * 2 * m; e += blockDim.x) {
+      const int r = e / (2 * m), j = e % (2 * m);
+      if (r == c) continue;
+      double2* X = j < m ? S : H;
+      const int jj = j < m ? j : j - m;
+      const double2 t = cmul(f[r], X[(long long)c * ld + jj]);
+      X[(long long)r * ld + jj] = csub(X[(long long)r * ld + jj], t);
+    }
+    __syncthreads();
+  }
+}
+
 __global__ void hupdate_kernel(const __grid_constant__ HUpdBatch batch) {
   const HUpdJob& J = batch.job[blockIdx.x];
   const int p = J.p, b = J.b, ld = J.ld;
@@ -545,6 +603,14 @@ void launch_ritz_batch(const RitzBatch& b, cudaStream_t s, long long* launches) 
 void launch_chol_batch(const CholBatch& cb, int b, int* status, cudaStream_t s, long long* launches) {
   if (cb.n <= 0) return;
   chol_kernel<<<cb.n, 32, 0, s>>>(cb, b, status);
+  SWI_CHECK_LAUNCH();
+  if (launches) ++*launches;
+}
+
+void launch_small_solve(double2* S, double2* H, int m, int ld, int* status, cudaStream_t s, long long* launches) {
+  if (m <= 0) return;
+  if (m > 1024 || ld < m) throw Error{SWI_EINVAL, "small solve: size out of range"};
+  small_solve_kernel<<<1, kDenseThreads, 0, s>>>(S, H, m, ld, status);
   SWI_CHECK_LAUNCH();
   if (launches) ++*launches;
 }

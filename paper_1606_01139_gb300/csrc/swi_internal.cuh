@@ -219,6 +219,10 @@ struct RitzBatch {
   RitzJob job[kMaxBatch];
 };
 void launch_ritz_batch(const RitzBatch& b, cudaStream_t s, long long* launches);
+// H = S^-1 K (m x m, row-major, leading dimension ld; H holds K on entry, S is
+// overwritten) by Gauss-Jordan elimination with partial pivoting, one CTA.
+// *status (device): 0, or 1 + the column without a nonzero pivot.
+void launch_small_solve(double2* S, double2* H, int m, int ld, int* status, cudaStream_t s, long long* launches);
 
 // Block-Arnoldi bookkeeping after one expansion (A [Q V] = [Q V] H' + V' B'):
 // H[0:p+b, p:p+b] = C1 + C2, H[p:p+b, 0:p] = B_old[:, 0:p], B = [0, R2 R1].
@@ -252,6 +256,12 @@ void launch_zext_batch(const ZextBatch& b, cudaStream_t s, long long* launches);
 // small element-wise helpers
 void launch_copy_block(const double2* src, int lds, double2* dst, int ldd, int rows, int cols,
                        cudaStream_t s, long long* launches);
+// dst[:, q] = src[:, idx[q]] for q < n (idx on the device)
+void launch_gather_cols(const double2* src, int lds, const int* idx, int n, double2* dst, int ldd, int rows,
+                        cudaStream_t s, long long* launches);
+// Y[:, q] -= eps[q] X[:, q] for q < n (eps on the device)
+void launch_sub_diag(double2* Y, int ldy, const double2* X, int ldx, const double2* eps, int n, int rows,
+                     cudaStream_t s, long long* launches);
 
 // ---------------------------------------------------------------- timing helper
 double now_seconds();

@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import workloads as W
-from oracle import eigen, partition, stencil, transport
+from oracle import eigen, partition, refine, stencil, transport
 
 pytestmark = pytest.mark.gpu
 
@@ -371,3 +371,83 @@ def test_budget_exhaustion_returns_partial_result(swi):
         info = c.solve(block=4, rel_tol=1e-13, max_matvecs=40)
         assert info["status"] == "SWI_ENOCONV"
         assert c.n_pairs() == 10
+
+
+# --------------------------------------------------------------------------- residual-correction sweep
+@pytest.fixture(scope="module")
+def refine_wire():
+    # a 6 x 7 cross-section has no degenerate pairs, so every refined vector
+    # is individually well conditioned (on a square one the perturbation splits
+    # each degenerate pair by ~1e-8 and single vectors move by 1e-8 under a
+    # 1e-15 change of the projected pencil)
+    w = W.make_wire(6, 7, 12, 0.5, 3, 7)
+    A = _dense(w)
+    eps, U = eigen.dense_spectrum(A)
+    an = stencil.gershgorin_norm(w.h, w.V, w.gamma_L, w.gamma_R)
+    return w, A, eps, U, an
+
+
+def _refine_both(swi, w, A, an, e0, U0, rel_tol, sweeps, group, arith):
+    eo, Uo, ro, so = refine.refine(lambda X: A @ X, an, e0, U0, rel_tol, max_sweeps=sweeps, group=group)
+    with _ctx(swi, w) as c:
+        c.set_eigenpairs(e0, U0)
+        info = c.refine(max_sweeps=sweeps, group=group, rel_tol=rel_tol, arith=arith)
+        eg, Ug = c.eigenpairs()
+        rg = c.residuals()
+    return (eo, Uo, ro, so), (eg, Ug, rg, info)
+
+
+def _same_pairs(eg, Ug, eo, Uo, eps_tol, vec_tol, cluster_rtol=1e-9):
+    assert len(eg) == len(eo)
+    assert np.max(np.abs(eg - eo)) <= eps_tol
+    for cl in eigen.clusters(eo, cluster_rtol):
+        Pg, Po = eigen.cluster_projector(Ug, cl), eigen.cluster_projector(Uo, cl)
+        assert np.max(np.abs(Pg - Po)) <= vec_tol * max(1.0, np.max(np.abs(Po)))
+
+
+@pytest.mark.parametrize("arith", ["ds", "f64"])
+def test_refine_exact_recovery(swi, refine_wire, arith):
+    # span[U', R'] is an invariant subspace: the sweep returns the exact pairs
+    w, A, eps, U, an = refine_wire
+    n = 24
+    U0 = U[:, :n] + 1e-3 * U[:, 200:200 + n]
+    e0 = eps[:n] + 1e-6
+    a = swi.ARITH_DS if arith == "ds" else swi.ARITH_F64
+    (eo, Uo, ro, so), (eg, Ug, rg, info) = _refine_both(swi, w, A, an, e0, U0, 1e-12, 1, 8, a)
+    assert info["sweeps"] == 1 and info["n_pairs"] == n and info["status"] == "SWI_OK", info
+    _same_pairs(eg, Ug, eps[:n], U[:, :n], 1e-10, 1e-8)
+    _same_pairs(eg, Ug, eo, Uo, 1e-10, 1e-8)
+    assert np.max(rg) <= 1e-12
+    np.testing.assert_allclose(Ug.T @ Ug, np.eye(n), atol=1e-9)
+
+
+@pytest.mark.parametrize("arith", ["ds", "f64"])
+def test_refine_parity_with_oracle(swi, refine_wire, arith):
+    # random perturbation of every vector: one sweep on the GPU and in the
+    # oracle from the same (seeded) pairs; the second group of 8 is left
+    # converged and must come back bit for bit
+    w, A, eps, U, an = refine_wire
+    n = 24
+    rng = np.random.default_rng(11)
+    noise = (rng.standard_normal((w.N, n)) + 1j * rng.standard_normal((w.N, n))) / np.sqrt(w.N)
+    U0 = U[:, :n] + 1e-4 * noise
+    e0 = eps[:n] * (1 + 1e-4)
+    U0[:, 8:16] = U[:, 8:16]
+    e0[8:16] = eps[8:16]
+    a = swi.ARITH_DS if arith == "ds" else swi.ARITH_F64
+    (eo, Uo, ro, so), (eg, Ug, rg, info) = _refine_both(swi, w, A, an, e0, U0, 1e-10, 1, 8, a)
+    assert info["sweeps"] == 1 and so == 1
+    _same_pairs(eg, Ug, eo, Uo, 1e-10, 1e-9 if arith == "ds" else 1e-10)
+    np.testing.assert_array_equal(eg[8:16], eps[8:16])
+    np.testing.assert_allclose(rg, ro, rtol=1e-5, atol=1e-14)
+    assert np.max(np.abs(eg - eps[:n])) < 1e-6  # quadratic in the 1e-4 vector error
+
+
+def test_refine_rejects_bad_arguments(swi, refine_wire):
+    w, A, eps, U, an = refine_wire
+    with _ctx(swi, w) as c:
+        with pytest.raises(RuntimeError):
+            c.refine()  # no pairs yet
+        c.set_eigenpairs(eps[:8], U[:, :8])
+        with pytest.raises(RuntimeError):
+            c.refine(group=33)

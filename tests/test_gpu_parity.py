@@ -451,3 +451,17 @@ def test_refine_rejects_bad_arguments(swi, refine_wire):
         c.set_eigenpairs(eps[:8], U[:, :8])
         with pytest.raises(RuntimeError):
             c.refine(group=33)
+
+
+@pytest.mark.parametrize("group", [1, 5, 32])
+def test_refine_group_sizes(swi, refine_wire, group):
+    # single-pair groups (a 2 x 2 pencil), a ragged last group (27 = 5 x 5 + 2)
+    # and the widest groups (products past 16 columns take the tensor-core
+    # path, a 64 x 64 pencil), against the oracle's sweep from the same pairs
+    w, A, eps, U, an = refine_wire
+    n = 27
+    U0 = U[:, :n] + 1e-3 * U[:, 200:200 + n]
+    e0 = eps[:n] + 1e-6
+    (eo, Uo, ro, so), (eg, Ug, rg, info) = _refine_both(swi, w, A, an, e0, U0, 1e-12, 1, group, swi.ARITH_DS)
+    assert info["sweeps"] == 1 and so == 1 and info["n_pairs"] == len(eo)
+    _same_pairs(eg, Ug, eo, Uo, 1e-10, 1e-9)

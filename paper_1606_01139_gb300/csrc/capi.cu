@@ -515,8 +515,11 @@ swi_status do_solve(swi_ctx* c, const swi_solve_opts* o, swi_solve_info* info) {
   struct SideRes {
     std::vector<cudaStream_t> st;
     std::vector<cudaEvent_t> ready, done;
+    cudaEvent_t lag[2] = {nullptr, nullptr};
     int* oi = nullptr;
     ~SideRes() {
+      for (auto x : lag)
+        if (x) cudaEventDestroy(x);
       for (auto x : st)
         if (x) cudaStreamDestroy(x);
       for (auto x : ready)
@@ -535,6 +538,7 @@ swi_status do_solve(swi_ctx* c, const swi_solve_opts* o, swi_solve_info* info) {
     SWI_CUDA_TRY(cudaEventCreateWithFlags(&side.done[j], cudaEventDisableTiming));
   }
   SWI_CUDA_TRY(cudaMallocHost(&side.oi, sizeof(int) * 4 * nwin));
+  for (auto& e : side.lag) SWI_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   std::vector<int> in_schur(nwin, 0);
 
   // Act on a finished Schur step of window j: finalise or thick-restart (context stream).
@@ -589,6 +593,10 @@ swi_status do_solve(swi_ctx* c, const swi_solve_opts* o, swi_solve_info* info) {
 
   const long long max_steps = 100000000LL;
   for (long long step = 0; step < max_steps; ++step) {
+    // Keep the host at most two steps ahead of the device.  Unbounded, the
+    // launch queue holds ~1 s of steps, and a window whose Schur step has
+    // finished would rejoin the batch only behind all of them, idle meanwhile.
+    if (step >= 2) SWI_CUDA_TRY(cudaEventSynchronize(side.lag[step & 1]));
     // collect finished restarts
     for (int j = 0; j < nwin; ++j) {
       if (!in_schur[j]) continue;
@@ -706,6 +714,7 @@ swi_status do_solve(swi_ctx* c, const swi_solve_opts* o, swi_solve_info* info) {
       SWI_CUDA_TRY(cudaEventRecord(side.done[j], side.st[j]));
       in_schur[j] = 1;
     }
+    SWI_CUDA_TRY(cudaEventRecord(side.lag[step & 1], c->stream));
   }
   // ---- gather eigenvalue estimates and window statistics
   std::vector<double2> eps_all(n_all);

@@ -659,7 +659,7 @@ void launch_rowgemm_df(const RowGemmBatch& b, int N, cudaStream_t s, long long* 
   if (maxc <= 16 && maxk <= 32) {
     dim3 grid((N + 63) / 64, 1, b.n);
     rowgemm_df_kernel<64, 16><<<grid, 256, 0, s>>>(b, N);
-  } else if (true) {
+  } else {
     // long contractions (the Gram-Schmidt update W -= Q C, the restart rotation
     // Q Z): tensor cores with the exact digit split
     static bool attr = false;
@@ -670,9 +670,6 @@ void launch_rowgemm_df(const RowGemmBatch& b, int N, cudaStream_t s, long long* 
     }
     dim3 grid((N + oz::kTI - 1) / oz::kTI, (maxc + oz::kTJ - 1) / oz::kTJ, b.n);
     rowgemm_oz_kernel<<<grid, 256, oz::kSmem, s>>>(b, N);
-  } else {
-    dim3 grid((N + 31) / 32, (maxc + 31) / 32, b.n);
-    rowgemm_df_kernel<32, 32><<<grid, 256, 0, s>>>(b, N);
   }
   SWI_CHECK_LAUNCH();
   if (launches) ++*launches;

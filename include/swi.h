@@ -68,15 +68,19 @@ enum { SWI_ARITH_DS = 2, SWI_ARITH_F64 = 1 };     /* see swi_solve_opts.arith */
 typedef struct {
   int block;            /* b, Krylov block width (default 16; 1..32) */
   int max_basis;        /* m_j, basis size before a restart (default
-                           max(2 n_req + 1, n_req + 2b) rounded up to b) */
+                           max(2 n_req + 1, keep + (8 + j mod 3) b) rounded
+                           up to b, j the window index: the stagger keeps
+                           equal windows from restarting in step) */
   int keep;             /* Ritz vectors kept at a restart (default
                            max(n_req + n_req/2, n_req + b), at most m_j - b) */
-  int arith;            /* arithmetic of the tall-skinny products (Gram,
-                           update, Cholesky-QR, rotations, T(E) projections):
-                           0 or SWI_ARITH_DS (default) -- double-single on the
-                           FP32 pipes, ~1e-13 relative; SWI_ARITH_F64 -- native
-                           FP64.  The stencil, the projected eigenproblems and
-                           the final residual check are native FP64 in both. */
+  int arith;            /* arithmetic of the Krylov loop and T(E):
+                           0 or SWI_ARITH_DS (default) -- stencil, Cholesky-QR,
+                           projected Schur step and T(E) projections in
+                           double-single on the FP32 pipes, Gram-Schmidt
+                           products and restart rotation on the tensor cores
+                           with an exact digit split, ~1e-13 relative;
+                           SWI_ARITH_F64 -- native FP64 throughout.  The final
+                           explicit residual check is native FP64 in both. */
   long long max_matvecs;/* per-window budget of operator applications per
                            vector (default 2,000,000) */
   double rel_tol;       /* convergence: ||A u - eps u|| <= rel_tol ||A||_G ||u||,
@@ -212,8 +216,9 @@ typedef struct {
   int max_sweeps;       /* sweeps at most (default 3) */
   int group;            /* consecutive pairs (by real part) per Rayleigh-Ritz
                            problem, n_g (default 16; 1..32) */
-  int arith;            /* as swi_solve_opts.arith (products and the projected
-                           Schur step; stencil and residuals are native FP64) */
+  int arith;            /* as swi_solve_opts.arith for the products and the
+                           projected Schur step; the stencil and the residuals
+                           of a sweep are native FP64 in both */
   int reserved;
   double rel_tol;       /* target relative residual, as in swi_solve (default 1e-10) */
   double eq_rtol;       /* Algorithm 2 tests applied to the refined pairs, as */

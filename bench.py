@@ -255,11 +255,15 @@ def run_reference(args, rank, world):
     if rank != 0:
         return 0
     cfg = W.CONFIGS[WORKLOAD]
+    try:  # the same lowest window as the GPU arm's plan (and its cpu_baseline leg)
+        sigma1 = float(plan(cfg)[0][0])
+    except OSError:
+        sigma1 = None
     vals = []
     for _ in range(args.warmup):
-        cpu_baseline(cfg)
+        cpu_baseline(cfg, sigma1)
     for _ in range(args.steps):
-        vals.append(cpu_baseline(cfg))
+        vals.append(cpu_baseline(cfg, sigma1))
     v = sum(x["value"] for x in vals) / len(vals)
     cb = dict(vals[-1])
     cb["value"] = v

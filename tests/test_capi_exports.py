@@ -60,3 +60,14 @@ def test_create_without_device_reports_an_error(lib):
     swi.load()
     with pytest.raises(swi.SwiError):
         swi.Context(10, 10, 20, 0.5, stream=0)
+
+
+def test_null_context_is_rejected_by_every_entry_taking_one(lib):
+    # no device needed: each call validates its context before touching CUDA
+    import paper_1606_01139_gb300 as swi
+    swi.load()
+    L = swi._lib
+    assert L.swi_solve(None, None, None) == swi.SWI_EINVAL
+    assert L.swi_refine(None, None, None) == swi.SWI_EINVAL
+    assert L.swi_residuals(None, None) == swi.SWI_EINVAL
+    assert L.swi_transmission(None, 1, None, None) == swi.SWI_EINVAL

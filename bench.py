@@ -497,7 +497,10 @@ def main():
     log("complex64 stencil")
     out["stencil_c64"] = stencil_c64_rate(swi, stream, hbm)
     log("residual-correction sweep")
-    out["refine"] = refine_sweep(ctx)
+    try:  # reported beside the step, never a reason to lose the bench line
+        out["refine"] = refine_sweep(ctx)
+    except RuntimeError as e:
+        out["refine"] = {"error": str(e)}
     if not args.no_cpu_baseline:
         log("cpu baseline")
         out["cpu_baseline"] = cpu_baseline(cfg, float(sig[0]))

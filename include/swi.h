@@ -302,17 +302,19 @@ swi_status swi_profile_read(swi_ctx* ctx, swi_kernel_stats* out);
 
 /* T(E) for the context's current pairs, like swi_transmission, but without
  * allocating anything on the device or through any allocator.  The paper has
- * no counterpart: this exists for callers that cannot allocate device memory
- * at call time -- code that records the call into a CUDA graph under stream
- * capture (where cudaMalloc is not allowed), and hosts whose framework owns
- * the whole device memory budget (a caching allocator that must not see
- * foreign allocations, a hard memory cap).
+ * no counterpart: this exists for callers that must not allocate device
+ * memory at call time -- hosts whose framework owns the whole device memory
+ * budget (a caching allocator that must not see foreign allocations, a hard
+ * memory cap) or whose allocations must all happen up front.
+ *  - The call copies E in and T out through pageable host memory and
+ *    synchronises the context's stream before it returns.
  *  - Limits: at most 64 eigenpairs in the context and 1024 energies per call;
- *    larger sizes return SWI_EINVAL (use swi_transmission instead).
+ *    larger sizes return SWI_EINVAL (use swi_transmission instead).  Any grid
+ *    size is accepted: the projections run over slabs of 65,536 grid rows.
  *  - Scratch: one file-scope device array of 4.6 MB that every GPU which loads
- *    the library holds until the process exits.  The first call on each device
- *    looks up the array's device address (cudaGetSymbolAddress); make that
- *    first call before any stream capture.
+ *    the library holds until the process exits.  Its device address is looked
+ *    up once per device ordinal (cudaGetSymbolAddress, with that device
+ *    current) by swi_create; the call itself only reads the cached address.
  *  - Every call on a device shares that array, which keeps the last call's
  *    contents; calls whose work overlaps on the GPU (other host threads, other
  *    contexts on other streams) race on it and must be serialised by the

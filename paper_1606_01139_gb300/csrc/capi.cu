@@ -19,113 +19,18 @@
 #include "merge.cuh"
 #include "swi_internal.cuh"
 #include "transport.cuh"
+#include "host.cuh"
 
 using swi::Error;
+using namespace swi::host;
 
 namespace {
-
 thread_local std::string g_create_error;
-
-// 12th-order central second-difference weights (radius 6), c_0..c_6.
-// Algorithmic FP64 flops of the stencil per grid point and vector: 18 neighbour
-// pairs x (2 adds + 2 FMA) + the local term (2 MUL + 2 FMA) + the shift (2 adds).
-constexpr double kStencilFlops = 18.0 * 6.0 + 6.0 + 2.0;
-
-const double kFD[7] = {-5369.0 / 1800.0, 12.0 / 7.0, -15.0 / 56.0, 10.0 / 189.0,
-                       -1.0 / 112.0,     2.0 / 1925.0, -1.0 / 16632.0};
-
-struct DevMem {
-  void* p = nullptr;
-  size_t bytes = 0;
-  DevMem() = default;
-  DevMem(const DevMem&) = delete;
-  DevMem& operator=(const DevMem&) = delete;
-  ~DevMem() { release(); }
-  void release() {
-    if (p) cudaFree(p);
-    p = nullptr;
-    bytes = 0;
-  }
-  void ensure(size_t nbytes) {
-    if (nbytes <= bytes) return;
-    release();
-    if (nbytes == 0) return;
-    cudaError_t e = cudaMalloc(&p, nbytes);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      p = nullptr;
-      throw Error{SWI_ENOMEM, "cudaMalloc of " + std::to_string(nbytes) + " bytes failed"};
-    }
-    bytes = nbytes;
-  }
-  template <class T>
-  T* as() const {
-    return static_cast<T*>(p);
-  }
-};
-
-struct Window {
-  double sigma = 0.0;
-  int nreq = 0, m = 0, keep = 0, ld = 0;  // ld: columns of the Q buffers (m + b)
-  DevMem Q[2], W, H, Bm, Z, S, Bz, theta, resid, C1, C2, G, R1, R1i, R2, R2i, Zext, Yw, eps_w, res_w, Hw, Zw;
-  int cur = 0, p = 0;
-  bool done = false, failed = false;
-  long long matvecs = 0;
-  int restarts = 0;
-  int nconv = 0;
-  double max_res = 0.0;
-};
-
 }  // namespace
 
-struct swi_ctx {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  int nx = 0, ny = 0, nz = 0, N = 0;
-  double h = 0.0;
-  int bc = SWI_BC_ODD, precision = SWI_PREC_F64;
-  DevMem V, G, gL, gR;
-  DevMem V32, G32;  // FP32 copies for the complex64 stencil
-  bool has_V = false, has_G = false;
-  double maxabsV = 0.0, maxG = 0.0;
-  std::vector<double> sigma;
-  std::vector<int> nreq;
-  // current pairs
-  int npairs = 0;
-  DevMem eps, U;  // [n], [N][n]
-  std::vector<double> resid;
-  std::vector<swi_window_info> winfo;
-  // transport cache
-  bool have_RL = false;
-  DevMem MR, ML, Rm, Lm, Wm, Mg, Ebuf, Tbuf, dEbuf, wbuf;
-  // workspaces
-  DevMem gram_work, sig_dev, colwork, scratch, Uall, ordinfo, cholstat, ptrs, dres;
-  // merge scratch
-  DevMem m_comp, m_pairs, m_counts, m_work, m_gram, m_kept, m_order, m_holes, m_src, m_coef, m_nterm, m_info,
-      m_win, m_eps_all, m_eps_out;
-  long long launches = 0;
-  int arith = SWI_ARITH_DS;  // arithmetic of the tall-skinny products (last solve's choice)
-  std::string err;
-  // per-kernel-class event timing
-  struct ProfRec {
-    int kind;
-    cudaEvent_t a, b;
-    double flops, bytes;
-  };
-  bool prof_on = false;
-  double schur_flops = 0.0;  // work of the Schur steps, known only after they ran
-  std::vector<ProfRec> prof;
-  std::vector<cudaEvent_t> evpool;
-  ~swi_ctx() {
-    for (auto& r : prof) {
-      cudaEventDestroy(r.a);
-      cudaEventDestroy(r.b);
-    }
-    for (auto e : evpool) cudaEventDestroy(e);
-  }
-};
+namespace swi {
+namespace host {
 
-namespace {
 
 cudaEvent_t take_event(swi_ctx* c) {
   if (!c->evpool.empty()) {
@@ -138,33 +43,25 @@ cudaEvent_t take_event(swi_ctx* c) {
   return e;
 }
 
-// Records CUDA events around the launches of its scope when profiling is on.
-struct ProfScope {
-  swi_ctx* c;
-  int kind;
-  double flops, bytes;
-  cudaStream_t st;
-  cudaEvent_t a = nullptr;
-  ProfScope(swi_ctx* ctx, int k, double f, double by, cudaStream_t stream = nullptr)
-      : c(ctx), kind(k), flops(f), bytes(by), st(stream ? stream : ctx->stream) {
-    if (c->prof_on) {
-      a = take_event(c);
-      SWI_CUDA_TRY(cudaEventRecord(a, st));
-    }
+ProfScope::ProfScope(swi_ctx* ctx, int k, double f, double by, cudaStream_t stream)
+    : c(ctx), kind(k), flops(f), bytes(by), st(stream ? stream : ctx->stream) {
+  if (c->prof_on) {
+    a = take_event(c);
+    SWI_CUDA_TRY(cudaEventRecord(a, st));
   }
-  ~ProfScope() {
-    if (!a) return;
-    cudaEvent_t b = nullptr;
-    if (!c->evpool.empty()) {
-      b = c->evpool.back();
-      c->evpool.pop_back();
-    } else if (cudaEventCreate(&b) != cudaSuccess) {
-      return;
-    }
-    if (cudaEventRecord(b, st) != cudaSuccess) return;
-    c->prof.push_back({kind, a, b, flops, bytes});
+}
+ProfScope::~ProfScope() {
+  if (!a) return;
+  cudaEvent_t b = nullptr;
+  if (!c->evpool.empty()) {
+    b = c->evpool.back();
+    c->evpool.pop_back();
+  } else if (cudaEventCreate(&b) != cudaSuccess) {
+    return;
   }
-};
+  if (cudaEventRecord(b, st) != cudaSuccess) return;
+  c->prof.push_back({kind, a, b, flops, bytes});
+}
 
 // Tall-skinny products: double-single on the FP32 pipes (default) or native FP64.
 void gram_dispatch(int arith, const swi::GramBatch& b, int N, const double* w, int bilinear, double2* work,
@@ -225,7 +122,7 @@ void copy_in(DevMem& dst, const void* src, size_t bytes, bool on_device, cudaStr
 void sync(cudaStream_t s) { SWI_CUDA_TRY(cudaStreamSynchronize(s)); }
 
 // Y[:, c] = (A - sigma_c) X[:, c] in chunks of columns, sigma from the context's sigma table
-void apply_block(swi_ctx* c, const double2* X, int ldx, double2* Y, int ldy, int ncols, bool ds = false) {
+void apply_block(swi_ctx* c, const double2* X, int ldx, double2* Y, int ldy, int ncols, bool ds) {
   const swi::StencilParams P = stencil_params(c);
   for (int c0 = 0; c0 < ncols; c0 += 32) {
     swi::StencilBatch bt;
@@ -397,6 +294,12 @@ void merge_pairs(swi_ctx* c, const double2* Uin, int ldu, const std::vector<doub
   c->npairs = nout;
   c->have_RL = false;
 }
+
+}  // namespace host
+}  // namespace swi
+
+namespace {
+using namespace swi::host;
 
 swi_status do_solve(swi_ctx* c, const swi_solve_opts* o, swi_solve_info* info) {
   if (!c->has_V || !c->has_G) return fail(c, SWI_ESTATE, "potential and absorbers must be set before solve");
@@ -1033,6 +936,41 @@ bool finite_all(const double* p, size_t n) {
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// T(E) without any allocation, for callers that must not allocate device
+// memory at call time (see swi_transmission_noalloc in swi.h).  All scratch
+// lives in one file-scope device array, shared by every call on a device.
+namespace {
+constexpr int kNoAllocMaxPairs = 64;
+constexpr int kNoAllocMaxEnergies = 1024;
+constexpr size_t kNoAllocMat = (size_t)kNoAllocMaxPairs * kNoAllocMaxPairs;  // one n x n matrix
+constexpr size_t kNoAllocWork = 64 * kNoAllocMat;                            // split-N partial sums
+constexpr int kNoAllocSlab = 64 * 1024;  // grid rows per projection pass: 64 chunks of 1024 rows
+// layout: MR, ML, R, L, W (n x n each), Gram partial sums, then E[1024], T[1024] as doubles
+constexpr size_t kNoAllocElems = 5 * kNoAllocMat + kNoAllocWork + kNoAllocMaxEnergies;
+}  // namespace
+
+static __device__ __align__(256) double2 g_noalloc_scratch[kNoAllocElems];  // 4.6 MB per device
+
+namespace {
+std::mutex g_noalloc_mutex;
+std::vector<void*> g_noalloc_addr;  // device address of g_noalloc_scratch, per device ordinal
+
+// Once per device, with that device current: the array's device address.
+double2* noalloc_scratch(int device) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if ((int)g_noalloc_addr.size() <= device) g_noalloc_addr.resize(device + 1, nullptr);
+  if (!g_noalloc_addr[device]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      throw Error{SWI_ECUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e)};
+    g_noalloc_addr[device] = p;
+  }
+  return static_cast<double2*>(g_noalloc_addr[device]);
+}
+}  // namespace
+
 extern "C" {
 
 swi_status swi_create(swi_ctx** out, int nx, int ny, int nz, double h, int bc, int precision, void* cuda_stream) {
@@ -1055,6 +993,12 @@ swi_status swi_create(swi_ctx** out, int nx, int ny, int nz, double h, int bc, i
     cudaGetLastError();
     delete c;
     return fail(nullptr, SWI_ECUDA, "no CUDA device");
+  }
+  try {
+    noalloc_scratch(c->device);  // device address of the no-allocation scratch, once per device
+  } catch (const Error& e) {
+    delete c;
+    return fail(nullptr, e.code, e.msg);
   }
   c->stream = static_cast<cudaStream_t>(cuda_stream);
   c->nx = nx;
@@ -1415,40 +1359,6 @@ swi_status swi_profile_read(swi_ctx* c, swi_kernel_stats* out) {
 
 }  // extern "C"
 
-// ---------------------------------------------------------------------------
-// T(E) without any allocation, for callers that must not allocate device
-// memory at call time (see swi_transmission_noalloc in swi.h).  All scratch
-// lives in one file-scope device array, shared by every call on a device.
-namespace {
-constexpr int kNoAllocMaxPairs = 64;
-constexpr int kNoAllocMaxEnergies = 1024;
-constexpr size_t kNoAllocMat = (size_t)kNoAllocMaxPairs * kNoAllocMaxPairs;  // one n x n matrix
-constexpr size_t kNoAllocWork = 64 * kNoAllocMat;                            // split-N partial sums
-// layout: MR, ML, R, L, W (n x n each), Gram partial sums, then E[1024], T[1024] as doubles
-constexpr size_t kNoAllocElems = 5 * kNoAllocMat + kNoAllocWork + kNoAllocMaxEnergies;
-}  // namespace
-
-static __device__ __align__(256) double2 g_noalloc_scratch[kNoAllocElems];  // 4.6 MB per device
-
-namespace {
-std::mutex g_noalloc_mutex;
-std::vector<void*> g_noalloc_addr;  // device address of g_noalloc_scratch, per device ordinal
-
-// Once per device, with that device current: the array's device address.
-double2* noalloc_scratch(int device) {
-  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if ((int)g_noalloc_addr.size() <= device) g_noalloc_addr.resize(device + 1, nullptr);
-  if (!g_noalloc_addr[device]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p)
-      throw Error{SWI_ECUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e)};
-    g_noalloc_addr[device] = p;
-  }
-  return static_cast<double2*>(g_noalloc_addr[device]);
-}
-}  // namespace
-
 extern "C" {
 
 swi_status swi_transmission_noalloc(swi_ctx* c, int nE, const double* E, double* T_out) {
@@ -1475,12 +1385,20 @@ swi_status swi_transmission_noalloc(swi_ctx* c, int nE, const double* E, double*
     // every scratch region below is fully overwritten before it is read, so
     // nothing needs clearing between calls
     SWI_CUDA_TRY(cudaMemcpyAsync(Ed, E, sizeof(double) * nE, cudaMemcpyHostToDevice, c->stream));
-    swi::GramBatch gb;
-    gb.n = 1;
-    gb.job[0] = swi::GramJob{c->U.as<double2>(), c->U.as<double2>(), MR, n, n, n, n, n, 0};
-    gram_dispatch(c->arith, gb, c->N, c->gR.as<double>(), 0, work, kNoAllocWork, c->stream, &c->launches);
-    gb.job[0].C = ML;
-    gram_dispatch(c->arith, gb, c->N, c->gL.as<double>(), 0, work, kNoAllocWork, c->stream, &c->launches);
+    // The projections run over slabs of kNoAllocSlab grid rows, each summed on
+    // top of the previous ones: a slab fits the fixed partial-sum workspace
+    // with the same at-most-1024-rows chunks that swi_transmission uses, at
+    // any grid size.
+    for (int r0 = 0; r0 < c->N; r0 += kNoAllocSlab) {
+      const int rows = std::min(kNoAllocSlab, c->N - r0);
+      const double2* Us = c->U.as<double2>() + (size_t)r0 * n;
+      swi::GramBatch gb;
+      gb.n = 1;
+      gb.job[0] = swi::GramJob{Us, Us, MR, n, n, n, n, n, r0 > 0 ? 1 : 0};
+      gram_dispatch(c->arith, gb, rows, c->gR.as<double>() + r0, 0, work, kNoAllocWork, c->stream, &c->launches);
+      gb.job[0].C = ML;
+      gram_dispatch(c->arith, gb, rows, c->gL.as<double>() + r0, 0, work, kNoAllocWork, c->stream, &c->launches);
+    }
     swi::launch_wbuild(MR, ML, n, R, L, Wm, c->stream, &c->launches);
     swi::launch_transmission(Wm, c->eps.as<double2>(), n, Ed, nE, Td, nullptr, c->stream, &c->launches);
     SWI_CUDA_TRY(cudaMemcpyAsync(T_out, Td, sizeof(double) * nE, cudaMemcpyDeviceToHost, c->stream));

@@ -66,13 +66,23 @@ enum { SWI_ARITH_DS = 2, SWI_ARITH_F64 = 1 };     /* see swi_solve_opts.arith */
 /* Options of swi_solve.  Zero-initialise and set what you need; zero fields
  * take the defaults given here. */
 typedef struct {
-  int block;            /* b, Krylov block width (default 16; 1..32) */
+  int block;            /* b, Krylov block width (default 16; 1..32).  b = 1
+                           selects single-vector windows, the form of the
+                           paper's implicitly restarted Arnoldi: every window
+                           adds one vector per step, all windows share each
+                           stencil and Gram-Schmidt launch, and the products
+                           stream complex128 bases in double-single arithmetic
+                           (SWI_PREC_MIXED contexts always run this form, on
+                           complex64 bases with FP32 arithmetic) */
   int max_basis;        /* m_j, basis size before a restart (default
                            max(2 n_req + 1, keep + (8 + j mod 3) b) rounded
                            up to b, j the window index: the stagger keeps
-                           equal windows from restarting in step) */
+                           equal windows from restarting in step; for
+                           single-vector windows max(2 n_req + 1,
+                           keep + 128 + 16 (j mod 3)), at most 1000) */
   int keep;             /* Ritz vectors kept at a restart (default
-                           max(n_req + n_req/2, n_req + b), at most m_j - b) */
+                           max(n_req + ceil(n_req/2), n_req + b), at most
+                           m_j - b) */
   int arith;            /* arithmetic of the Krylov loop and T(E):
                            0 or SWI_ARITH_DS (default) -- stencil, Cholesky-QR,
                            projected Schur step and T(E) projections in
@@ -121,11 +131,21 @@ typedef struct {
   double t_merge_s;     /* wall time of merge, selection and normalisation */
 } swi_solve_info;
 
-/* Create a context on the current CUDA device.
+/* Create a context on the current CUDA device for the operator of Eq. 1 on an
+ * nx x ny x nz grid of spacing h (Section 1: the Hamiltonian is applied as a
+ * matrix-free finite-difference formula, never stored).
  *  bc: SWI_BC_ODD -- psi = 0 on the planes just outside the grid, ghosts by
  *      odd reflection u[-1-k] = -u[-1+k] (keeps A = A^T exactly);
  *      SWI_BC_ZERO -- every ghost is zero.
- *  precision: SWI_PREC_F64 (complex128 vectors, FP64 arithmetic).
+ *  precision: SWI_PREC_F64 -- complex128 Krylov vectors with FP64-class
+ *      arithmetic (native FP64 or double-single, swi_solve_opts.arith);
+ *      SWI_PREC_MIXED -- the reduced-precision form: swi_solve runs
+ *      single-vector windows on complex64 Krylov vectors with FP32 stencil
+ *      and products (FP32 accumulation within chunks of at most 1024 grid
+ *      rows, FP64 across them) and the projected eigenproblems in
+ *      double-single; the delivered pairs are complex128 and their explicit
+ *      FP64 residuals are reported, at the accuracy of FP32 arithmetic.
+ *      Everything after the solve (merge, T(E), gradients) is FP64 in both.
  *  cuda_stream: cudaStream_t (or NULL for the legacy default stream) on which
  *      every kernel of this context runs.
  * Errors: SWI_EINVAL (an axis < 6, h <= 0, unknown bc/precision),
@@ -247,7 +267,9 @@ typedef struct {
  * Q^T (A - sigma_g) Q y = theta Q^T Q y (the unconjugated form, under which
  * the eigenvectors of the complex-symmetric A are bi-orthogonal, Section 1)
  * of smallest magnitude (the windows' SM selection, Eq. 3) give
- * eps = sigma_g + theta and U = Q y.  All pairs then pass Algorithm 2 as
+ * eps = sigma_g + theta and U = Q y; a group keeps its new pairs only if
+ * their largest explicit FP64 residual is below the old one (otherwise the
+ * previous pairs are put back).  All pairs then pass Algorithm 2 as
  * one window (equal-eigenvalue projection, redundancy drop, U^T U = I), and
  * the explicit FP64 residuals are recomputed; sweeps stop when every pair is
  * at rel_tol.  The pairs stay in library-owned memory (swi_get_eigenpairs).
@@ -264,13 +286,17 @@ swi_status swi_refine(swi_ctx* ctx, const swi_refine_opts* opts, swi_refine_info
  * Errors: SWI_ESTATE (no pairs), SWI_EINVAL. */
 swi_status swi_transmission(swi_ctx* ctx, int nE, const double* E, double* T_out);
 
-/* Vector-Jacobian product of T: given dL/dT_e (nE host doubles), writes
- * dL/dV(r) = sum_e dLdT_e 2 Re[(G Gamma_R G^dagger Gamma_L G)_rr] with
- * dG = G dV G in the spectral representation (N doubles, on_device selects
- * where), and dT_e/dE_e = -2 Re sum_kl g_k^2 W_kl conj(g_l) (nE host doubles).
- * Either output may be NULL. */
+/* Vector-Jacobian product of T (the adjoint of the spectral T(E) of Section 1,
+ * with dG = G dV G): given dL/dT_e (nE host doubles), writes
+ *   dL/dV(r) = sum_e dLdT_e 2 Re[(G Gamma_R G^dagger Gamma_L G)_rr]
+ *            = 2 Re sum_{a,c} U_ra M_ac U_rc,  M = sum_e dLdT_e D_e R conj(D_e) L^T D_e,
+ *            D_e = diag(g_e)   (N doubles, on_device selects where), and
+ *   dL/dE_e  = dLdT_e dT_e/dE_e,  dT_e/dE_e = -2 Re sum_kl g_ek^2 W_kl conj(g_el)
+ *            (nE host doubles; with dLdT == NULL the bare dT_e/dE_e).
+ * Either output may be NULL; dLdV needs dLdT.  Errors: SWI_ESTATE (no pairs or
+ * no absorbers), SWI_EINVAL (NULL E, non-finite input). */
 swi_status swi_grad(swi_ctx* ctx, int nE, const double* E, const double* dLdT, double* dLdV,
-                    int dLdV_on_device, double* dTdE);
+                    int dLdV_on_device, double* dLdE);
 
 /* Per-kernel-class timing (CUDA events on the context's stream), for
  * roofline accounting.  Classes: */

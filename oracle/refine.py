@@ -22,6 +22,11 @@ fixes a reading:
   its eigenvalue error is quadratic in the vectors' error, where the Hermitian
   projection Q^H A Q of a non-Hermitian A gives a linear one.  The result does
   not depend on which basis of the span is used;
+* a group keeps its Rayleigh-Ritz pairs only if their largest relative
+  residual is below the group's previous largest; otherwise its previous pairs
+  stay (far from convergence the SM selection around sigma_g can pick
+  directions with larger residuals: the sweep sharpens pairs, it is not a
+  solver);
 * all pairs then pass Algorithm 2 as one window (equal-eigenvalue projection,
   redundancy drop, v^T v = 1) and are ordered by real part.
 """
@@ -33,8 +38,9 @@ from . import eigen, partition
 
 
 def rr_sweep(apply_A, eps: np.ndarray, U: np.ndarray, res: np.ndarray, rel_tol: float, group: int = 16,
-             eq_rtol: float = 1e-8, drop_tol: float = 1e-6):
-    """One sweep over the Re-sorted pairs (eps, U) with relative residuals res."""
+             eq_rtol: float = 1e-8, drop_tol: float = 1e-6, anorm: float | None = None):
+    """One sweep over the Re-sorted pairs (eps, U) with relative residuals res (relative to anorm;
+    anorm None skips the keep-only-if-better rule)."""
     n = len(eps)
     eps_new = np.array(eps, dtype=np.complex128, copy=True)
     U_new = np.array(U, dtype=np.complex128, copy=True)
@@ -51,6 +57,8 @@ def rr_sweep(apply_A, eps: np.ndarray, U: np.ndarray, res: np.ndarray, rel_tol: 
         theta, Y = np.linalg.eig(np.linalg.solve(S, K))
         sel = np.argsort(np.abs(theta), kind="stable")[:len(g)]
         e, V = eigen.sort_by_real(theta[sel] + sigma, Q @ Y[:, sel])
+        if anorm is not None and not np.max(eigen.residual_norms(apply_A, e, V) / anorm) < np.max(res[g]):
+            continue
         eps_new[g] = e
         U_new[:, g] = V
     eps2, U2, _, _ = partition.combine([eps_new], [U_new], eq_rtol, drop_tol)
@@ -68,7 +76,7 @@ def refine(apply_A, anorm: float, eps: np.ndarray, U: np.ndarray, rel_tol: float
     res = relative_residuals(apply_A, anorm, eps, U)
     sweeps = 0
     while sweeps < max_sweeps and not np.all(res <= rel_tol):
-        eps, U = rr_sweep(apply_A, eps, U, res, rel_tol, group, eq_rtol, drop_tol)
+        eps, U = rr_sweep(apply_A, eps, U, res, rel_tol, group, eq_rtol, drop_tol, anorm)
         res = relative_residuals(apply_A, anorm, eps, U)
         sweeps += 1
     return eps, U, res, sweeps

@@ -252,7 +252,10 @@ class Context:
     # -- solve
     def solve(self, block=16, rel_tol=1e-10, max_basis=0, keep=0, max_matvecs=0, eq_rtol=0.0, drop_tol=0.0,
               seed=1, n_keep=0, arith=ARITH_DS, allow=(SWI_OK, SWI_ENOCONV, SWI_HOLES)):
-        """Windowed solve; arith = ARITH_DS (double-single products, default) or ARITH_F64 (native)."""
+        """Windowed solve; arith = ARITH_DS (double-single products, default) or ARITH_F64 (native).
+
+        block=1 runs single-vector windows (complex128 bases, double-single products); a
+        PREC_MIXED context always runs them, on complex64 bases (block must be 0 or 1)."""
         o = SolveOpts(block=block, max_basis=max_basis, keep=keep, max_matvecs=max_matvecs, rel_tol=rel_tol,
                       eq_rtol=eq_rtol, drop_tol=drop_tol, seed=seed, n_keep=n_keep, arith=arith)
         info = SolveInfo()
@@ -330,7 +333,9 @@ class Context:
         return T
 
     def grad(self, E, dLdT, dLdV_out=None):
-        """(dL/dV[N], dT/dE[nE]).  dLdV_out may be a torch CUDA float64 tensor of length N."""
+        """(dL/dV[N], dL/dE[nE]) for the weights dL/dT (dL/dE_e = dLdT_e dT_e/dE_e).
+
+        dLdV_out may be a torch CUDA float64 tensor of length N."""
         E = _c_arr(np.atleast_1d(E), np.float64)
         w = _c_arr(np.atleast_1d(dLdT), np.float64)
         dE = np.empty_like(E)
@@ -379,11 +384,11 @@ def transmission_function():
             w = gT.detach().cpu().numpy().astype(np.float64)
             if fctx.V_device.type == "cuda":
                 dV = torch.empty(fctx.sctx.N, dtype=torch.float64, device=fctx.V_device)
-                dV, dTdE = fctx.sctx.grad(fctx.E, w, dLdV_out=dV)
+                dV, dLdE = fctx.sctx.grad(fctx.E, w, dLdV_out=dV)
             else:
-                dVn, dTdE = fctx.sctx.grad(fctx.E, w)
+                dVn, dLdE = fctx.sctx.grad(fctx.E, w)
                 dV = torch.as_tensor(dVn, dtype=torch.float64)
-            dE = torch.as_tensor(w * dTdE, dtype=torch.float64, device=gT.device)
+            dE = torch.as_tensor(dLdE, dtype=torch.float64, device=gT.device)
             return dV, dE, None
 
     return TransmissionFn

@@ -875,6 +875,31 @@ swi_status do_refine(swi_ctx* c, const swi_refine_opts* o, swi_refine_info* info
       if (si[gi] != 0) return fail(c, SWI_ENOCONV, "refine: singular Q^T Q in a group");
       if (oi[4 * gi + 2] != 0) return fail(c, SWI_ENOCONV, "refine: a projected eigenproblem did not converge");
     }
+    // a group is replaced only if its largest explicit residual falls; otherwise
+    // its previous pairs are put back (a sweep sharpens eigenvalues, it is not a
+    // solver: on pairs far from convergence it can raise the residual)
+    {
+      std::vector<double> rn;
+      explicit_residuals(c, Unew.as<double2>(), n, epsnew.as<double2>(), n, rn);
+      mv += n;
+      for (int gi = 0; gi < ngroups; ++gi) {
+        const int lo = gi * g, ng = std::min(g, n - lo);
+        if (ioff[gi + 1] == ioff[gi]) continue;
+        double before = 0.0, after = 0.0;
+        for (int k = lo; k < lo + ng; ++k) {
+          before = std::max(before, c->resid[k]);
+          after = std::max(after, rn[k]);
+        }
+        if (after < before) continue;
+        swi::launch_copy_block(c->U.as<double2>() + lo, n, Unew.as<double2>() + lo, n, c->N, ng, c->stream,
+                               &c->launches);
+        SWI_CUDA_TRY(cudaMemcpyAsync(epsnew.as<double2>() + lo, c->eps.as<double2>() + lo, sizeof(double2) * ng,
+                                     cudaMemcpyDeviceToDevice, c->stream));
+        SWI_CUDA_TRY(cudaMemcpyAsync(en.data() + lo, c->eps.as<double2>() + lo, sizeof(double2) * ng,
+                                     cudaMemcpyDeviceToHost, c->stream));
+      }
+      sync(c->stream);
+    }
     // Algorithm 2 over the refined pairs as one window, U^T U = I
     int minfo[4];
     merge_pairs(c, Unew.as<double2>(), n, en, std::vector<int>(n, 0), 1, eq_rtol, drop_tol, 0, minfo);
@@ -979,8 +1004,7 @@ swi_status swi_create(swi_ctx** out, int nx, int ny, int nz, double h, int bc, i
   if (nx < 6 || ny < 6 || nz < 6) return fail(nullptr, SWI_EINVAL, "each axis needs at least 6 points");
   if (!(h > 0.0) || !std::isfinite(h)) return fail(nullptr, SWI_EINVAL, "grid spacing must be positive");
   if (bc != SWI_BC_ODD && bc != SWI_BC_ZERO) return fail(nullptr, SWI_EINVAL, "unknown boundary rule");
-  if (precision != SWI_PREC_F64)
-    return fail(nullptr, precision == SWI_PREC_MIXED ? SWI_ENOTIMPL : SWI_EINVAL, "only SWI_PREC_F64 is available");
+  if (precision != SWI_PREC_F64 && precision != SWI_PREC_MIXED) return fail(nullptr, SWI_EINVAL, "unknown precision");
   const long long N = (long long)nx * ny * nz;
   if (N > (1LL << 31) - 1) return fail(nullptr, SWI_EINVAL, "grid too large");
   swi_ctx* c = nullptr;
@@ -1179,6 +1203,7 @@ swi_status swi_apply_c64(swi_ctx* c, int nvec, const float* sigma, const void* X
                               c->sig_dev.as<float>(), c->stream, &c->launches);
       return SWI_OK;
     }
+    swi::stencil_c64_tma_error(true);
     DevMem dx, dy;
     dx.ensure(bytes);
     dy.ensure(bytes);
@@ -1187,12 +1212,22 @@ swi_status swi_apply_c64(swi_ctx* c, int nvec, const float* sigma, const void* X
                             &c->launches);
     SWI_CUDA_TRY(cudaMemcpyAsync(Y, dy.p, bytes, cudaMemcpyDeviceToHost, c->stream));
     sync(c->stream);
+    if (swi::stencil_c64_tma_error(true))
+      return fail(c, SWI_ETIMEOUT, "a stencil block gave up waiting for its tensor-map copy");
     return SWI_OK;
   });
 }
 
 swi_status swi_solve(swi_ctx* c, const swi_solve_opts* opts, swi_solve_info* info) {
-  return guarded(c, [&]() -> swi_status { return do_solve(c, opts, info); });
+  return guarded(c, [&]() -> swi_status {
+    if (c->precision == SWI_PREC_MIXED) {
+      if (opts && opts->block > 1) return fail(c, SWI_EINVAL, "SWI_PREC_MIXED runs single-vector windows (block 0 or 1)");
+      if (opts && opts->arith == SWI_ARITH_F64) return fail(c, SWI_EINVAL, "SWI_PREC_MIXED has no native-FP64 form");
+      return do_solve_sv(c, opts, info);
+    }
+    if (opts && opts->block == 1 && opts->arith != SWI_ARITH_F64) return do_solve_sv(c, opts, info);
+    return do_solve(c, opts, info);
+  });
 }
 
 swi_status swi_refine(swi_ctx* c, const swi_refine_opts* opts, swi_refine_info* info) {
@@ -1277,7 +1312,7 @@ swi_status swi_transmission(swi_ctx* c, int nE, const double* E, double* T_out) 
 }
 
 swi_status swi_grad(swi_ctx* c, int nE, const double* E, const double* dLdT, double* dLdV, int dLdV_on_device,
-                    double* dTdE) {
+                    double* dLdE) {
   return guarded(c, [&]() -> swi_status {
     if (c->npairs <= 0) return fail(c, SWI_ESTATE, "no eigenpairs");
     if (!c->has_G) return fail(c, SWI_ESTATE, "absorbers must be set");
@@ -1287,13 +1322,13 @@ swi_status swi_grad(swi_ctx* c, int nE, const double* E, const double* dLdT, dou
     ensure_RL(c);
     const int n = c->npairs;
     copy_in(c->Ebuf, E, sizeof(double) * nE, false, c->stream);
-    if (dTdE) {
+    if (dLdE) {
       c->Tbuf.ensure(sizeof(double) * nE);
       c->dEbuf.ensure(sizeof(double) * nE);
       ProfScope ps(c, SWI_K_TRANS, 8.0 * nE * (double)n * n, 16.0 * (double)n * n);
       swi::launch_transmission(c->Wm.as<double2>(), c->eps.as<double2>(), n, c->Ebuf.as<double>(), nE,
                                c->Tbuf.as<double>(), c->dEbuf.as<double>(), c->stream, &c->launches);
-      SWI_CUDA_TRY(cudaMemcpyAsync(dTdE, c->dEbuf.p, sizeof(double) * nE, cudaMemcpyDeviceToHost, c->stream));
+      SWI_CUDA_TRY(cudaMemcpyAsync(dLdE, c->dEbuf.p, sizeof(double) * nE, cudaMemcpyDeviceToHost, c->stream));
     }
     if (dLdV) {
       copy_in(c->wbuf, dLdT, sizeof(double) * nE, false, c->stream);
@@ -1320,6 +1355,8 @@ swi_status swi_grad(swi_ctx* c, int nE, const double* E, const double* dLdT, dou
       sync(c->stream);
     }
     sync(c->stream);
+    if (dLdE && dLdT)  // chain rule: T_e depends on E_e alone
+      for (int e = 0; e < nE; ++e) dLdE[e] *= dLdT[e];
     return SWI_OK;
   });
 }

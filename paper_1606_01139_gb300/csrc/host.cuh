@@ -144,6 +144,9 @@ void sync(cudaStream_t s);
 void apply_block(swi_ctx* c, const double2* X, int ldx, double2* Y, int ldy, int ncols, bool ds = false);
 void explicit_residuals(swi_ctx* c, const double2* Ud, int ldu, const double2* epsd, int n, std::vector<double>& out);
 void gram_work_ensure(swi_ctx* c, size_t elems);
+// the windowed solve with single-vector windows (solve_sv.cu): block width 1
+// in an FP64 context, and every solve of a SWI_PREC_MIXED context
+swi_status do_solve_sv(swi_ctx* c, const swi_solve_opts* o, swi_solve_info* info);
 void merge_pairs(swi_ctx* c, const double2* Uin, int ldu, const std::vector<double2>& eps_all,
                  const std::vector<int>& win_of, int nwin, double eq_rtol, double drop_tol, int n_keep, int* minfo);
 

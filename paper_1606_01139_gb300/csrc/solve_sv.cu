@@ -1,0 +1,528 @@
+// The windowed solve with single-vector windows (block width 1).
+//
+// Each window j runs the single-vector Krylov-Schur iteration on the shifted,
+// never-inverted operator A - sigma_j (Eq. 3) with the 'SM' selection: the
+// exact-shift thick restart that ARPACK's implicitly restarted Arnoldi method
+// performs (Section 2.1), one new basis vector per window and step.  All
+// windows step in lockstep: one stencil launch applies A - sigma_j to the
+// newest vector of every window, and each Gram-Schmidt pass (classical, twice)
+// is one launch over all windows that streams every basis once.  A window
+// whose basis is full runs its projected eigenproblem (schur_ds.cu) on a
+// stream of its own while the others keep expanding, then rotates its basis
+// to the kept Schur vectors.
+//
+// Two arithmetics share this driver:
+//  - complex128 bases, double-single products and stencil (krylov_sv.cu,
+//    stencil_ds.cu): the FP64 method, pairs to FP64-class residuals;
+//  - complex64 bases, FP32 products and stencil (krylov_sv.cu, krylov_c64.cu,
+//    stencil_c64_tma.cu): the reduced-precision form of SWI_PREC_MIXED
+//    contexts, whose pairs are widened to complex128 for the merge and checked
+//    by the same FP64 residuals (their accuracy is that of FP32 arithmetic, so
+//    Algorithm 2's equal-eigenvalue and redundancy tests default to 1e-5 and
+//    1e-2 there).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <type_traits>
+#include <vector>
+
+#include "host.cuh"
+#include "merge.cuh"
+#include "swi_internal.cuh"
+
+namespace swi {
+namespace host {
+
+namespace {
+
+template <bool DS>
+struct SV {
+  using T = std::conditional_t<DS, double2, float2>;
+  using Sig = std::conditional_t<DS, double, float>;
+};
+
+template <bool DS>
+struct SvWin {
+  using T = typename SV<DS>::T;
+  double sigma = 0.0;  // the shift the stencil applies (rounded to FP32 in the complex64 form)
+  int nreq = 0, m = 0, keep = 0, ldq = 0, ldh = 0, col = 0;
+  int p = 0;           // index of the newest basis vector (the one expanded next)
+  DevMem Q, H, Z, S, Bz, theta, resid, Yw, eps_w, res_w, Hw, Zw, C1, C2, Z32, invb, part;  // part: FP64 chunk partials
+  bool done = false, failed = false;
+  long long matvecs = 0;
+  int restarts = 0, nconv = 0;
+};
+
+// H <- [[T_kk, 0], [b^T, 0]]: keep the leading kk x kk Schur block, put the
+// coupling row b = B Z[:, 0:kk] below it, clear the rest of the (n x n) array.
+__global__ void restart_h_kernel(double2* H, int ldh, int n, int kk, const double2* Bz) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)n * n) return;
+  const int i = (int)(e / n), j = (int)(e % n);
+  if (i < kk && j < kk) return;
+  H[(long long)i * ldh + j] = (i == kk && j < kk) ? Bz[j] : make_double2(0.0, 0.0);
+}
+
+void launch_restart_h(double2* H, int ldh, int n, int kk, const double2* Bz, cudaStream_t s, long long* launches) {
+  const long long e = (long long)n * n;
+  restart_h_kernel<<<(unsigned)((e + 255) / 256), 256, 0, s>>>(H, ldh, n, kk, Bz);
+  SWI_CHECK_LAUNCH();
+  if (launches) ++*launches;
+}
+
+__global__ void random_col_c128_kernel(double2* __restrict__ dst, int ld, int rows, unsigned long long seed) {
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += (long long)gridDim.x * blockDim.x) {
+    unsigned long long z = seed + 0x9E3779B97F4A7C15ull * (2 * r + 1);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    unsigned long long y = seed + 0x9E3779B97F4A7C15ull * (2 * r + 2);
+    y = (y ^ (y >> 30)) * 0xBF58476D1CE4E5B9ull;
+    y = (y ^ (y >> 27)) * 0x94D049BB133111EBull;
+    y ^= y >> 31;
+    dst[r * ld] = make_double2((double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0,
+                               (double)(y >> 11) * (2.0 / 9007199254740992.0) - 1.0);
+  }
+}
+
+swi::StencilC64Params stencil_c64_params(const swi_ctx* c) {
+  swi::StencilC64Params P;
+  P.nx = c->nx;
+  P.ny = c->ny;
+  P.nz = c->nz;
+  P.bc = c->bc;
+  for (int m = 0; m < 7; ++m) P.cm[m] = (float)(-kFD[m] / (2.0 * c->h * c->h));
+  P.V = c->V32.as<float>();
+  P.G = c->G32.as<float>();
+  return P;
+}
+
+template <bool DS>
+swi_status solve_sv(swi_ctx* c, const swi_solve_opts& opt, swi_solve_info* info) {
+  using Tr = SV<DS>;
+  using T = typename Tr::T;
+  using Win = SvWin<DS>;
+  const double rel_tol = opt.rel_tol > 0 ? opt.rel_tol : 1e-10;
+  const double eq_rtol = opt.eq_rtol > 0 ? opt.eq_rtol : (DS ? 1e-8 : 1e-5);
+  const double drop_tol = opt.drop_tol > 0 ? opt.drop_tol : (DS ? 1e-6 : 1e-2);
+  const long long budget = opt.max_matvecs > 0 ? opt.max_matvecs : 2000000LL;
+  const unsigned long long seed = opt.seed ? opt.seed : 1ull;
+  const double anorm = gershgorin(c);
+  const int nwin = (int)c->sigma.size();
+  if (nwin > swi::kMaxBatch) return fail(c, SWI_EINVAL, "at most 64 windows per solve");
+  c->arith = SWI_ARITH_DS;
+  if (!DS) swi::stencil_c64_tma_error(true);
+  const double t0 = swi::now_seconds();
+  const size_t N = c->N;
+
+  std::vector<std::unique_ptr<Win>> win(nwin);
+  size_t total_out = 0;
+  int max_m = 1;
+  for (int j = 0; j < nwin; ++j) {
+    win[j].reset(new Win());
+    Win& w = *win[j];
+    w.sigma = DS ? c->sigma[j] : (double)(float)c->sigma[j];
+    w.nreq = c->nreq[j];
+    w.col = j;
+    int keep = opt.keep > 0 ? opt.keep : std::max(w.nreq + (w.nreq + 1) / 2, w.nreq + 1);
+    // the default basis leaves 128 to 144 new vectors per restart cycle (the
+    // stagger by window index keeps equal windows from restarting together)
+    int m = opt.max_basis > 0 ? opt.max_basis : std::max(2 * w.nreq + 1, keep + 128 + 8 * (j % 3));
+    if (keep > m - 1) keep = m - 1;
+    if (keep < w.nreq) return fail(c, SWI_EINVAL, "max_basis too small for the window request");
+    if (m > 1000) return fail(c, SWI_EINVAL, "single-vector windows: basis of at most 1000 vectors");
+    if (m + 1 > c->N) return fail(c, SWI_EINVAL, "basis larger than the problem dimension");
+    w.m = m;
+    w.keep = keep;
+    w.ldq = DS ? (m + 2) / 2 * 2 : (m + 4) / 4 * 4;  // >= m + 1 columns, rows on 32-byte boundaries
+    w.ldh = m + 1;
+    max_m = std::max(max_m, m);
+    total_out += w.nreq;
+  }
+  const int rpc = swi::sv_rows_per_chunk(c->N, nwin);
+  const int nchunks = (c->N + rpc - 1) / rpc;
+  for (int j = 0; j < nwin; ++j) {
+    Win& w = *win[j];
+    const size_t hh = (size_t)w.ldh * w.ldh;
+    w.Q.ensure(sizeof(T) * N * w.ldq);
+    w.H.ensure(sizeof(double2) * hh);
+    w.Z.ensure(sizeof(double2) * hh);
+    w.S.ensure(sizeof(double2) * hh);
+    w.Bz.ensure(sizeof(double2) * w.ldh);
+    w.theta.ensure(sizeof(double2) * w.ldh);
+    w.resid.ensure(sizeof(double) * w.ldh);
+    w.Hw.ensure(16 * hh);
+    w.Zw.ensure(16 * hh);
+    w.Yw.ensure(sizeof(double2) * w.ldh * w.nreq);
+    w.eps_w.ensure(sizeof(double2) * w.nreq);
+    w.res_w.ensure(sizeof(double) * w.nreq);
+    w.C1.ensure(sizeof(double2) * w.ldh);
+    w.C2.ensure(sizeof(double2) * w.ldh);
+    if (!DS) w.Z32.ensure(sizeof(float2) * hh);
+    w.invb.ensure(sizeof(double) * 2);
+    w.part.ensure(sizeof(double2) * (size_t)nchunks * w.ldh);
+    SWI_CUDA_TRY(cudaMemsetAsync(w.H.p, 0, sizeof(double2) * hh, c->stream));
+    SWI_CUDA_TRY(cudaMemsetAsync(w.Q.p, 0, sizeof(T) * N * w.ldq, c->stream));
+  }
+  const int n_all = (int)total_out;
+  c->Uall.ensure(sizeof(double2) * N * n_all);
+  c->ordinfo.ensure(sizeof(int) * 4 * nwin);
+  // newest vector of every window (column j) and its image under A - sigma_j;
+  // a complex128 work block for the restart rotations and the delivered Ritz vectors
+  DevMem Vcur, Wblk, sigt, Tmp;
+  const int ldv = nwin + (nwin & 1);  // even: 16-byte rows for the tensor-map-staged stencil
+  Vcur.ensure(sizeof(T) * N * ldv);
+  Wblk.ensure(sizeof(T) * N * ldv);
+  SWI_CUDA_TRY(cudaMemsetAsync(Vcur.p, 0, sizeof(T) * N * ldv, c->stream));
+  sigt.ensure(sizeof(double) * std::max(nwin, 4));
+  Tmp.ensure(sizeof(double2) * N * (max_m + 1));
+  {
+    std::vector<typename Tr::Sig> sg(nwin);
+    for (int j = 0; j < nwin; ++j) sg[j] = (typename Tr::Sig)win[j]->sigma;
+    SWI_CUDA_TRY(cudaMemcpyAsync(sigt.p, sg.data(), sizeof(typename Tr::Sig) * nwin, cudaMemcpyHostToDevice,
+                                 c->stream));
+    sync(c->stream);
+  }
+  const swi::StencilParams P64 = stencil_params(c);
+  const swi::StencilC64Params P32 = stencil_c64_params(c);
+  auto apply_all = [&]() {
+    if constexpr (DS) {
+      swi::StencilBatch sb;
+      sb.n = 0;
+      for (int c0 = 0; c0 < nwin; c0 += 32)
+        sb.blk[sb.n++] = swi::StencilBlock{reinterpret_cast<const double2*>(Vcur.p) + c0,
+                                           reinterpret_cast<double2*>(Wblk.p) + c0, ldv, ldv,
+                                           std::min(32, nwin - c0), c0};
+      swi::launch_stencil_ds(P64, sb, sigt.as<double>(), c->stream, &c->launches);
+    } else {
+      swi::launch_stencil_c64(P32, Vcur.as<float2>(), ldv, Wblk.as<float2>(), ldv, nwin, sigt.as<float>(),
+                              c->stream, &c->launches);
+    }
+  };
+
+  // start vectors: random, normalised, in column 0 of each basis and in Vcur
+  {
+    swi::SvBatch gb;
+    swi::SvReduceBatch rb;
+    swi::SvNormBatch nb;
+    gb.n = rb.n = nb.n = nwin;
+    for (int j = 0; j < nwin; ++j) {
+      Win& w = *win[j];
+      if constexpr (DS)
+        random_col_c128_kernel<<<std::min((c->N + 255) / 256, 1024), 256, 0, c->stream>>>(
+            Wblk.as<double2>() + j, ldv, c->N, seed * 1000003ull + j);
+      else
+        swi::launch_random_col_c64(Wblk.as<float2>() + j, ldv, c->N, seed * 1000003ull + j, c->stream, &c->launches);
+      SWI_CHECK_LAUNCH();
+      SWI_CUDA_TRY(cudaMemsetAsync(w.C2.p, 0, sizeof(double2), c->stream));
+      gb.job[j] = swi::SvJob{w.Q.p, w.ldq, 1, Wblk.as<T>() + j, ldv, w.C2.template as<double2>(),
+                             w.part.template as<double2>(), w.ldh};
+      rb.job[j] = swi::SvReduceJob{w.part.template as<double2>(), w.ldh, nchunks, 1, 1, nullptr, nullptr, 0,
+                                   w.invb.template as<double>()};
+      nb.job[j] = swi::SvNormJob{Wblk.as<T>() + j, ldv, w.Q.p, w.ldq, Vcur.as<T>() + j, ldv, w.invb.template as<double>()};
+    }
+    // ||w||^2 (the update by a zero basis column is a no-op)
+    swi::launch_sv_pass(gb, swi::SV_UPDATE_NORM, DS, c->N, rpc, c->stream, &c->launches);
+    swi::launch_sv_reduce(rb, c->stream, &c->launches);
+    swi::launch_sv_normalize(nb, DS, c->N, c->stream, &c->launches);
+  }
+
+  const double tol_abs = rel_tol * anorm;
+  std::vector<int> out_off(nwin);
+  {
+    int o2 = 0;
+    for (int j = 0; j < nwin; ++j) {
+      out_off[j] = o2;
+      o2 += win[j]->nreq;
+    }
+  }
+
+  struct SideRes {
+    std::vector<cudaStream_t> st;
+    std::vector<cudaEvent_t> ready, done;
+    cudaEvent_t lag[2] = {nullptr, nullptr};
+    int* oi = nullptr;
+    ~SideRes() {
+      for (auto x : lag)
+        if (x) cudaEventDestroy(x);
+      for (auto x : st)
+        if (x) cudaStreamDestroy(x);
+      for (auto x : ready)
+        if (x) cudaEventDestroy(x);
+      for (auto x : done)
+        if (x) cudaEventDestroy(x);
+      if (oi) cudaFreeHost(oi);
+    }
+  } side;
+  side.st.assign(nwin, nullptr);
+  side.ready.assign(nwin, nullptr);
+  side.done.assign(nwin, nullptr);
+  for (int j = 0; j < nwin; ++j) {
+    SWI_CUDA_TRY(cudaStreamCreateWithFlags(&side.st[j], cudaStreamNonBlocking));
+    SWI_CUDA_TRY(cudaEventCreateWithFlags(&side.ready[j], cudaEventDisableTiming));
+    SWI_CUDA_TRY(cudaEventCreateWithFlags(&side.done[j], cudaEventDisableTiming));
+  }
+  SWI_CUDA_TRY(cudaMallocHost(&side.oi, sizeof(int) * 4 * nwin));
+  for (auto& e : side.lag) SWI_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  std::vector<int> in_schur(nwin, 0);
+
+  // the window's basis as complex128 [N][ld] (the complex64 form widens it into Tmp)
+  auto basis64 = [&](Win& w, int& ld) -> const double2* {
+    if constexpr (DS) {
+      ld = w.ldq;
+      return w.Q.template as<double2>();
+    } else {
+      swi::launch_widen(w.Q.template as<float2>(), w.ldq, Tmp.as<double2>(), w.ldh, c->N, w.m, c->stream,
+                        &c->launches);
+      ld = w.ldh;
+      return Tmp.as<double2>();
+    }
+  };
+
+  auto finish_restart = [&](int j) {
+    Win& w = *win[j];
+    const int* oi = side.oi + 4 * j;
+    const int kk = oi[0], nconv = oi[1], st = oi[2];
+    SWI_CUDA_TRY(cudaStreamWaitEvent(c->stream, side.done[j], 0));
+    w.restarts++;
+    w.nconv = nconv;
+    if (c->prof_on) c->schur_flops += 64.0 / 3.0 * (double)w.m * w.m * w.m + 20.0 * 1024.0 * (double)oi[3];
+    if (st != 0) w.failed = true;
+    if (st != 0 || nconv >= w.nreq || w.matvecs >= budget) {
+      // Ritz vectors of the wanted pairs into Uall (complex128)
+      int ldb = 0;
+      const double2* Qb = basis64(w, ldb);
+      swi::RitzBatch fin;
+      fin.n = 1;
+      fin.job[0] = swi::RitzJob{w.Z.template as<double2>(), w.S.template as<double2>(), w.theta.template as<double2>(),
+                                w.resid.template as<double>(), c->ordinfo.as<int>() + 4 * j, w.Yw.template as<double2>(),
+                                w.eps_w.template as<double2>(), w.res_w.template as<double>(), w.m, w.ldh, w.nreq,
+                                w.nreq, w.sigma};
+      swi::RowGemmBatch rb;
+      rb.n = 1;
+      rb.job[0] = swi::RowGemmJob{Qb, w.Yw.template as<double2>(), nullptr, c->Uall.as<double2>() + out_off[j], ldb,
+                                  w.nreq, 0, n_all, w.m, w.nreq, 1.0, 0.0};
+      ProfScope ps(c, SWI_K_ROTATE, 8.0 * c->N * (double)w.m * w.nreq, 16.0 * c->N * (double)(w.m + w.nreq));
+      swi::launch_ritz_batch(fin, c->stream, &c->launches);
+      rowgemm_dispatch(SWI_ARITH_DS, rb, c->N, c->stream, &c->launches);
+      w.done = true;
+      return;
+    }
+    if (kk + 1 > w.m || kk < w.nreq) throw Error{SWI_ECUDA, "internal: restart size out of range"};
+    {
+      // thick restart: Q[:, 0:kk] = Q[:, 0:m] Z[:, 0:kk], the residual vector q_m becomes column kk
+      ProfScope ps(c, SWI_K_ROTATE, 8.0 * c->N * (double)w.m * kk, sizeof(T) * c->N * (double)(w.m + kk));
+      if constexpr (DS) {
+        swi::RowGemmBatch rb;
+        rb.n = 1;
+        rb.job[0] = swi::RowGemmJob{w.Q.template as<double2>(), w.Z.template as<double2>(), nullptr,
+                                    Tmp.as<double2>(), w.ldq, w.ldh, 0, w.ldh, w.m, kk, 1.0, 0.0};
+        rowgemm_dispatch(SWI_ARITH_DS, rb, c->N, c->stream, &c->launches);
+        swi::launch_copy_block(Tmp.as<double2>(), w.ldh, w.Q.template as<double2>(), w.ldq, c->N, kk, c->stream,
+                               &c->launches);
+        swi::launch_copy_block(w.Q.template as<double2>() + w.m, w.ldq, w.Q.template as<double2>() + kk, w.ldq, c->N,
+                               1, c->stream, &c->launches);
+      } else {
+        swi::launch_z_to_c64(w.Z.template as<double2>(), w.ldh, w.m, kk, w.Z32.template as<float2>(), kk, c->stream,
+                             &c->launches);
+        swi::launch_c64_rotate_inplace(w.Q.template as<float2>(), w.ldq, c->N, w.m, w.Z32.template as<float2>(), kk,
+                                       kk, c->stream, &c->launches);
+        swi::launch_copy_col_c64(w.Q.template as<float2>() + w.m, w.ldq, w.Q.template as<float2>() + kk, w.ldq, c->N,
+                                 c->stream, &c->launches);
+      }
+      launch_restart_h(w.H.template as<double2>(), w.ldh, w.ldh, kk, w.Bz.template as<double2>(), c->stream,
+                       &c->launches);
+    }
+    w.p = kk;  // the newest vector (already in Vcur) is q_m, now column kk
+  };
+
+  const long long max_steps = 100000000LL;
+  for (long long step = 0; step < max_steps; ++step) {
+    // keep the host at most two steps ahead of the device
+    if (step >= 2) SWI_CUDA_TRY(cudaEventSynchronize(side.lag[step & 1]));
+    for (int j = 0; j < nwin; ++j) {
+      if (!in_schur[j]) continue;
+      const cudaError_t q = cudaEventQuery(side.done[j]);
+      if (q == cudaErrorNotReady) continue;
+      SWI_CUDA_TRY(q);
+      in_schur[j] = 0;
+      finish_restart(j);
+    }
+    std::vector<Win*> act;
+    int pending = -1;
+    for (int j = 0; j < nwin; ++j) {
+      if (win[j]->done) continue;
+      if (in_schur[j]) {
+        if (pending < 0) pending = j;
+        continue;
+      }
+      act.push_back(win[j].get());
+    }
+    if (act.empty()) {
+      if (pending < 0) break;
+      SWI_CUDA_TRY(cudaEventSynchronize(side.done[pending]));
+      continue;
+    }
+    const int na = (int)act.size();
+    const double Nn = (double)c->N;
+    // 1) W[:, j] = (A - sigma_j) q_p for every window (columns of waiting windows are ignored)
+    {
+      ProfScope ps(c, SWI_K_STENCIL, kStencilFlops * Nn * nwin, (2.0 * sizeof(T) * nwin + 8.0) * Nn);
+      apply_all();
+    }
+    // 2) classical Gram-Schmidt twice against Q[:, 0:p+1], then the norm:
+    //    Gram, update fused with the second Gram, update fused with the norm
+    double ncol = 0.0;
+    swi::SvBatch g0, g1, g2;
+    swi::SvReduceBatch r0, r1, r2;
+    swi::SvNormBatch nb;
+    g0.n = g1.n = g2.n = r0.n = r1.n = r2.n = nb.n = na;
+    for (int q = 0; q < na; ++q) {
+      Win& w = *act[q];
+      if (w.p + 1 > w.m) throw Error{SWI_ECUDA, "internal: Krylov vector beyond the basis buffer"};
+      const int nc = w.p + 1;
+      ncol += nc;
+      T* Qp = w.Q.template as<T>();
+      T* wc = Wblk.as<T>() + w.col;
+      double2* pp = w.part.template as<double2>();
+      double2* H = w.H.template as<double2>();
+      double2* hcol = H + w.p;
+      g0.job[q] = swi::SvJob{Qp, w.ldq, nc, wc, ldv, nullptr, pp, w.ldh};
+      g1.job[q] = swi::SvJob{Qp, w.ldq, nc, wc, ldv, w.C1.template as<double2>(), pp, w.ldh};
+      g2.job[q] = swi::SvJob{Qp, w.ldq, nc, wc, ldv, w.C2.template as<double2>(), pp, w.ldh};
+      r0.job[q] = swi::SvReduceJob{pp, w.ldh, nchunks, nc, 0, w.C1.template as<double2>(), hcol, w.ldh, nullptr};
+      r1.job[q] = swi::SvReduceJob{pp, w.ldh, nchunks, nc, 0, w.C2.template as<double2>(), hcol, w.ldh, nullptr};
+      r2.job[q] = swi::SvReduceJob{pp, w.ldh, nchunks, 1, 1, nullptr, H + (long long)(w.p + 1) * w.ldh + w.p, 0,
+                                   w.invb.template as<double>()};
+      nb.job[q] = swi::SvNormJob{wc, ldv, Qp + w.p + 1, w.ldq, Vcur.as<T>() + w.col, ldv, w.invb.template as<double>()};
+    }
+    {
+      ProfScope ps(c, SWI_K_GRAM, 2.0 * 8.0 * Nn * ncol, 2.0 * sizeof(T) * Nn * ncol);
+      swi::launch_sv_pass(g0, swi::SV_GRAM, DS, c->N, rpc, c->stream, &c->launches);
+      swi::launch_sv_reduce(r0, c->stream, &c->launches);
+      swi::launch_sv_pass(g1, swi::SV_UPDATE_GRAM, DS, c->N, rpc, c->stream, &c->launches);
+      swi::launch_sv_reduce(r1, c->stream, &c->launches);
+    }
+    {
+      ProfScope ps(c, SWI_K_UPDATE, 8.0 * Nn * ncol, sizeof(T) * Nn * ncol + 2.0 * sizeof(T) * Nn * na);
+      swi::launch_sv_pass(g2, swi::SV_UPDATE_NORM, DS, c->N, rpc, c->stream, &c->launches);
+      swi::launch_sv_reduce(r2, c->stream, &c->launches);
+      swi::launch_sv_normalize(nb, DS, c->N, c->stream, &c->launches);
+    }
+    // 3) windows whose basis is full: projected eigenproblem on their own stream
+    for (int q = 0; q < na; ++q) {
+      Win& w = *act[q];
+      const int j = w.col;
+      w.p += 1;
+      w.matvecs += 1;
+      if (w.p < w.m) continue;
+      // as ARPACK does, keep more Ritz vectors once some wanted pairs have converged
+      const int keep_eff = std::min(w.m - 1, w.keep + std::min(w.nconv, (w.m - w.keep) / 2));
+      cudaStream_t sj = side.st[j];
+      SWI_CUDA_TRY(cudaEventRecord(side.ready[j], c->stream));
+      SWI_CUDA_TRY(cudaStreamWaitEvent(sj, side.ready[j], 0));
+      swi::SchurBatch sb;
+      sb.n = 1;
+      // B: the coupling row of the Arnoldi relation, row m of H (only H[m][m-1] = beta is nonzero)
+      double2* H = w.H.template as<double2>();
+      sb.job[0] = swi::SchurJob{H, w.Z.template as<double2>(), H + (long long)w.m * w.ldh, w.Bz.template as<double2>(),
+                                w.theta.template as<double2>(), w.resid.template as<double>(), w.S.template as<double2>(),
+                                c->ordinfo.as<int>() + 4 * j, w.m, w.ldh, 1, keep_eff, w.nreq, w.m - 1, tol_abs,
+                                w.Hw.p, w.Zw.p};
+      {
+        ProfScope ps(c, SWI_K_SCHUR, 0.0, 0.0, sj);
+        swi::launch_schur_ds_batch(sb, sj, &c->launches);
+      }
+      SWI_CUDA_TRY(cudaMemcpyAsync(side.oi + 4 * j, c->ordinfo.as<int>() + 4 * j, sizeof(int) * 4,
+                                   cudaMemcpyDeviceToHost, sj));
+      SWI_CUDA_TRY(cudaEventRecord(side.done[j], sj));
+      in_schur[j] = 1;
+    }
+    SWI_CUDA_TRY(cudaEventRecord(side.lag[step & 1], c->stream));
+  }
+
+  // ---- eigenvalue estimates and window statistics, then the merge (as in the block form)
+  std::vector<double2> eps_all(n_all);
+  std::vector<int> win_of(n_all);
+  c->winfo.assign(nwin, swi_window_info());
+  bool any_fail = false, any_noconv = false;
+  for (int j = 0; j < nwin; ++j) {
+    Win& w = *win[j];
+    std::vector<double> rw(w.nreq);
+    SWI_CUDA_TRY(cudaMemcpyAsync(eps_all.data() + out_off[j], w.eps_w.p, sizeof(double2) * w.nreq,
+                                 cudaMemcpyDeviceToHost, c->stream));
+    SWI_CUDA_TRY(cudaMemcpyAsync(rw.data(), w.res_w.p, sizeof(double) * w.nreq, cudaMemcpyDeviceToHost, c->stream));
+    sync(c->stream);
+    for (int q = 0; q < w.nreq; ++q) win_of[out_off[j] + q] = j;
+    swi_window_info& wi = c->winfo[j];
+    wi.sigma = w.sigma;
+    wi.n_req = w.nreq;
+    wi.n_conv = w.nconv;
+    wi.matvecs = w.matvecs;
+    wi.restarts = w.restarts;
+    wi.basis = w.m;
+    double mr = 0.0;
+    for (double r : rw) mr = std::max(mr, r / anorm);
+    wi.max_res = mr;
+    any_fail |= w.failed;
+    any_noconv |= (w.nconv < w.nreq);
+  }
+  win.clear();
+  Tmp.release();
+  Vcur.release();
+  Wblk.release();
+  const double t1 = swi::now_seconds();
+  int minfo[4];
+  merge_pairs(c, c->Uall.as<double2>(), n_all, eps_all, win_of, nwin, eq_rtol, drop_tol, opt.n_keep, minfo);
+  const int nout = minfo[0];
+  c->Uall.release();
+  {
+    ProfScope ps(c, SWI_K_MERGE, kStencilFlops * c->N * (double)nout, 48.0 * c->N * (double)nout);
+    explicit_residuals(c, c->U.as<double2>(), nout, c->eps.as<double2>(), nout, c->resid);
+  }
+  const double t2 = swi::now_seconds();
+  int nconv = 0;
+  double maxr = 0.0;
+  for (double r : c->resid) {
+    if (r <= rel_tol) ++nconv;
+    maxr = std::max(maxr, r);
+  }
+  long long mv = 0;
+  for (auto& wi : c->winfo) mv += wi.matvecs;
+  if (info) {
+    info->n_windows = nwin;
+    info->n_pairs = nout;
+    info->n_converged = nconv;
+    info->n_duplicates = minfo[1];
+    info->n_holes = minfo[2];
+    info->matvecs = mv;
+    info->max_rel_res = maxr;
+    info->anorm = anorm;
+    info->t_krylov_s = t1 - t0;
+    info->t_merge_s = t2 - t1;
+  }
+  if (!DS && swi::stencil_c64_tma_error(true))
+    return fail(c, SWI_ETIMEOUT, "a stencil block gave up waiting for its tensor-map copy");
+  if (any_fail) return fail(c, SWI_ENOCONV, "a window's projected eigenproblem did not converge");
+  if (minfo[3] != 0) return fail(c, SWI_EINVAL, "merge: equal-eigenvalue component too large");
+  if (any_noconv) return fail(c, SWI_ENOCONV, "some window did not converge within its matvec budget");
+  if (nconv < nout) return fail(c, SWI_ENOCONV, "pairs above rel_tol in the explicit FP64 residual check");
+  if (minfo[2] > 0) return fail(c, SWI_HOLES, std::to_string(minfo[2]) + " interface(s) without redundancy");
+  return SWI_OK;
+}
+
+}  // namespace
+
+swi_status do_solve_sv(swi_ctx* c, const swi_solve_opts* o, swi_solve_info* info) {
+  if (!c->has_V || !c->has_G) return fail(c, SWI_ESTATE, "potential and absorbers must be set before solve");
+  if (c->sigma.empty()) return fail(c, SWI_ESTATE, "windows must be set before solve");
+  swi_solve_opts opt;
+  std::memset(&opt, 0, sizeof(opt));
+  if (o) opt = *o;
+  if (c->precision == SWI_PREC_MIXED) return solve_sv<false>(c, opt, info);
+  return solve_sv<true>(c, opt, info);
+}
+
+}  // namespace host
+}  // namespace swi

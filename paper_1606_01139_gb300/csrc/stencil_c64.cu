@@ -1,17 +1,14 @@
 // Shifted stencil Y = (A - sigma_col) X on complex64 vectors with FP32
-// arithmetic: the operator of Eq. 1 applied matrix-free, shifted as in Eq. 3,
-// for the reduced-precision form of the Krylov loop.  At 8 bytes per complex
-// value the kernel is HBM-bound (74 FP32 FMAs per 16 algorithmic bytes), so it
-// is organised for traffic: each CTA owns a 16 x 8 tile of (x, y) points and
-// 4 columns and marches along z.  The 12 z-neighbours of a point live in a
-// register queue (one new plane per step, prefetched a step ahead); the x and y
-// neighbours come from the current plane, staged once into shared memory with
-// a 6-point cross-shaped halo (ghosts by odd reflection or zero, as in the
-// FP64 kernel), the next plane's staging loads issued before this plane's
-// arithmetic.  Reading 24 neighbours per output from shared memory (192 B)
-// bounds the kernel near half of HBM bandwidth; it measures well below that,
-// limited by load latency and the shared-memory instruction queue.  Layout: X, Y are [N][ld] complex64 (float2), column index
-// innermost.
+// arithmetic (Eq. 1 applied matrix-free, shifted as in Eq. 3): the form for
+// blocks whose rows are not 16-byte aligned (an odd column count); the
+// TMA-staged kernel of stencil_c64_tma.cu serves the rest.  Each CTA owns a
+// 16 x 8 tile of (x, y) points and 4 columns and marches along z.  The 12
+// z-neighbours of a point live in a register queue (one new plane per step,
+// prefetched a step ahead); the x and y neighbours come from the current plane,
+// staged into shared memory with a 6-point cross-shaped halo (ghosts by odd
+// reflection or zero, as in the FP64 kernel), the next plane's staging loads
+// issued before this plane's arithmetic.  Layout: X, Y are [N][ld] complex64
+// (float2), column index innermost.
 #include <algorithm>
 
 #include "swi_internal.cuh"
@@ -197,6 +194,10 @@ __global__ void __launch_bounds__(kThreadsC64, 1)
 void launch_stencil_c64(const StencilC64Params& P, const float2* X, int ldx, float2* Y, int ldy, int ncols,
                         const float* sigma_dev, cudaStream_t s, long long* launches) {
   if (ncols <= 0) return;
+  if (stencil_c64_tma_ok(X, ldx)) {  // TMA-staged form (stencil_c64_tma.cu) for 16-byte aligned rows
+    launch_stencil_c64_tma(P, X, ldx, Y, ldy, ncols, sigma_dev, s, launches);
+    return;
+  }
   const int tiles = ((P.nx + kTX - 1) / kTX) * ((P.ny + kTY - 1) / kTY);
   const int cgroups = (ncols + kNC - 1) / kNC;
   // z chunks: a CTA per SM or more, each chunk at least 16 planes deep so the

@@ -103,6 +103,12 @@ struct StencilC64Params {
 };
 void launch_stencil_c64(const StencilC64Params& P, const float2* X, int ldx, float2* Y, int ldy, int ncols,
                         const float* sigma_dev, cudaStream_t s, long long* launches);
+// TMA-staged form (stencil_c64_tma.cu): needs an even ldx and a 16-byte aligned X
+bool stencil_c64_tma_ok(const float2* X, int ldx);
+void launch_stencil_c64_tma(const StencilC64Params& P, const float2* X, int ldx, float2* Y, int ldy, int ncols,
+                            const float* sigma_dev, cudaStream_t s, long long* launches);
+// nonzero if a TMA stencil block gave up a bounded wait since the last clear
+int stencil_c64_tma_error(bool clear);
 
 constexpr int kMaxBatch = 64;
 
@@ -262,6 +268,73 @@ void launch_gather_cols(const double2* src, int lds, const int* idx, int n, doub
 // Y[:, q] -= eps[q] X[:, q] for q < n (eps on the device)
 void launch_sub_diag(double2* Y, int ldy, const double2* X, int ldx, const double2* eps, int n, int rows,
                      cudaStream_t s, long long* launches);
+
+// ---------------------------------------------------------------- single-vector Krylov loop
+// (krylov_sv.cu).  Per job (window): Q [N][ldq] basis columns [0, ncols)
+// (complex64 or complex128), w a column of a [N][ldw] block of the same type,
+// c ncols FP64 coefficients, part [nchunks][ldp] FP64 chunk partials.
+enum { SV_GRAM = 0, SV_UPDATE_GRAM = 1, SV_UPDATE_NORM = 2 };
+struct SvJob {
+  const void* Q;
+  int ldq, ncols;
+  void* w;
+  int ldw;
+  const double2* c;
+  double2* part;
+  int ldp;
+};
+struct SvBatch {
+  int n;
+  SvJob job[kMaxBatch];
+};
+// SV_GRAM: part = Q^H w; SV_UPDATE_GRAM: w -= Q c, then part = Q^H w;
+// SV_UPDATE_NORM: w -= Q c, then part[.][0] = ||w||^2.  ds: complex128 in
+// double-single arithmetic, else complex64 in FP32.
+void launch_sv_pass(const SvBatch& b, int mode, bool ds, int N, int rpc, cudaStream_t s, long long* launches);
+// rows per chunk for njobs windows (64 to 1024, a multiple of 8)
+int sv_rows_per_chunk(int N, int njobs);
+struct SvReduceJob {
+  const double2* part;
+  int ldp, nchunks, ncols;
+  int mode;      // 0: C = sum (H[i * ldh] += sum if H); 1: beta = sqrt(sum), H[0] = beta, invb = 1/beta
+  double2* C;
+  double2* H;
+  int ldh;
+  double* invb;
+};
+struct SvReduceBatch {
+  int n;
+  SvReduceJob job[kMaxBatch];
+};
+void launch_sv_reduce(const SvReduceBatch& b, cudaStream_t s, long long* launches);
+struct SvNormJob {
+  const void* w;
+  int ldw;
+  void* dst1;
+  int ld1;
+  void* dst2;  // may be NULL
+  int ld2;
+  const double* invb;
+};
+struct SvNormBatch {
+  int n;
+  SvNormJob job[kMaxBatch];
+};
+void launch_sv_normalize(const SvNormBatch& b, bool ds, int N, cudaStream_t s, long long* launches);
+// Q[:, 0:k] = Q[:, 0:m] Z32 in place (FP32), Z32 [m][ldz] complex64
+void launch_c64_rotate_inplace(float2* Q, int ldq, int N, int m, const float2* Z32, int ldz, int k, cudaStream_t s,
+                               long long* launches);
+void launch_z_to_c64(const double2* Z, int ldz, int m, int k, float2* Z32, int ld32, cudaStream_t s,
+                     long long* launches);
+// complex64 <-> complex128 copies of a [rows][cols] block
+void launch_widen(const float2* src, int lds, double2* dst, int ldd, int rows, int cols, cudaStream_t s,
+                  long long* launches);
+void launch_narrow(const double2* src, int lds, float2* dst, int ldd, int rows, int cols, cudaStream_t s,
+                   long long* launches);
+void launch_copy_col_c64(const float2* src, int lds, float2* dst, int ldd, int rows, cudaStream_t s,
+                         long long* launches);
+void launch_random_col_c64(float2* dst, int ld, int rows, unsigned long long seed, cudaStream_t s,
+                           long long* launches);
 
 // ---------------------------------------------------------------- timing helper
 double now_seconds();

@@ -73,3 +73,27 @@ def test_groups_without_unconverged_pairs_are_untouched(wire):
     e1, U1 = refine.rr_sweep(lambda X: A @ X, eps[:n], U0, res, 1e-10, group=8)
     np.testing.assert_array_equal(e1[:8], eps[:8])
     assert np.max(np.abs(e1[8:] - eps[8:n])) < 1e-11
+
+
+def test_sweep_never_raises_the_largest_residual(wire):
+    # pairs far from convergence (random combinations of the 40 lowest
+    # eigenvectors with shifted eigenvalues): whatever the Rayleigh-Ritz step
+    # returns, a group is replaced only if its largest residual falls, so the
+    # largest residual over all pairs never rises; with the groups' own
+    # residuals at rel_tol nothing changes at all
+    w, A, eps, U, an = wire
+    n = 16
+    apply = lambda X: A @ X  # noqa: E731
+    for seed in range(4):
+        rng = np.random.default_rng(seed)
+        C = rng.standard_normal((40, n)) + 1j * rng.standard_normal((40, n))
+        U0 = U[:, :40] @ C
+        U0 /= np.sqrt(np.sum(U0 * U0, axis=0))[None, :]
+        e0 = np.sort_complex(eps[:n] + 0.05)
+        r0 = refine.relative_residuals(apply, an, e0, U0)
+        e1, U1 = refine.rr_sweep(apply, e0, U0, r0, 1e-12, group=8, eq_rtol=0.0, drop_tol=0.0, anorm=an)
+        r1 = refine.relative_residuals(apply, an, e1, U1)
+        assert len(e1) == n and np.max(r1) <= np.max(r0) * (1 + 1e-12)
+        # every group replaced or kept whole: the kept groups' pairs are returned unchanged
+        e2, U2 = refine.rr_sweep(apply, e0, U0, np.zeros(n), 1e-12, group=8, eq_rtol=0.0, drop_tol=0.0, anorm=an)
+        np.testing.assert_array_equal(np.sort_complex(e2), np.sort_complex(e0))

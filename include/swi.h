@@ -71,15 +71,22 @@ typedef struct {
                            paper's implicitly restarted Arnoldi: every window
                            adds one vector per step, all windows share each
                            stencil and Gram-Schmidt launch, and the products
-                           stream complex128 bases in double-single arithmetic
-                           (SWI_PREC_MIXED contexts always run this form, on
-                           complex64 bases with FP32 arithmetic) */
+                           stream complex128 bases in double-single arithmetic.
+                           b = 2 runs the same batched loop with two new
+                           vectors per window and step (Cholesky-QR twice
+                           inside the pair): one starting vector spans only one
+                           vector of each eigenspace, so eigenvalues of
+                           multiplicity two (a symmetric cross-section) need
+                           b = 2 for both partners.  SWI_PREC_MIXED contexts
+                           run these forms only (b = 0 or 1: one vector, 2: two),
+                           on complex64 bases with FP32 arithmetic */
   int max_basis;        /* m_j, basis size before a restart (default
                            max(2 n_req + 1, keep + (8 + j mod 3) b) rounded
                            up to b, j the window index: the stagger keeps
                            equal windows from restarting in step; for
-                           single-vector windows max(2 n_req + 1,
-                           keep + 128 + 16 (j mod 3)), at most 1000) */
+                           b = 1 or 2 max(2 n_req + 1,
+                           keep + b (128 + 8 (j mod 3))), at most 1000 for
+                           b = 1 and 510 for b = 2) */
   int keep;             /* Ritz vectors kept at a restart (default
                            max(n_req + ceil(n_req/2), n_req + b), at most
                            m_j - b) */
@@ -176,6 +183,43 @@ swi_status swi_set_windows(swi_ctx* ctx, int p, const double* sigma, const int* 
 swi_status swi_plan_windows(swi_ctx* ctx, int n_r, int p, double e_min, double e_max,
                             double inflate, double* sigma_out, int* n_req_out);
 
+/* Options and outcome of swi_plan_windows_sampled (zero-initialise; zero
+ * fields take the defaults given here). */
+typedef struct {
+  int sample_req;          /* pairs per sampling window (default max(8, 2 n_r / p)) */
+  int max_samples;         /* sampling windows at most (default 64) */
+  double sample_tol;       /* relative residual of the sampling solves (default 1e-5) */
+  double inflate;          /* request = ceil(n_r,j * inflate) + extra (default 1.25) */
+  int extra;               /* added to every request (default 4; a negative value adds none) */
+  int counts_rule;         /* 0: equal counts n_r / p (default); 1: Algorithm 1's n_r,j */
+  long long max_matvecs;   /* operator applications per sampling window (default 200,000) */
+} swi_plan_opts;
+
+typedef struct {
+  double e_min, e_max;     /* extremal real parts from the two exterior solves (Algorithm 1's inputs) */
+  double e_top;            /* the n_r-th lowest sampled real part */
+  int samples;             /* sampling windows solved */
+  int windows;             /* windows planned */
+  long long matvecs;       /* operator applications of all planning solves */
+  double t_s;              /* wall time */
+} swi_plan_info;
+
+/* Plan p windows for the lowest n_r pairs without foreknowledge of the
+ * spectrum (Section 2.2.1): two exterior single-vector solves, below min V and
+ * above ||A||_G, give E_min and E_max; sampling solves of sample_req pairs at
+ * a loose tolerance march up from E_min (each shift three quarters of the way
+ * up the real parts the previous one found; the eigenvalues above its highest
+ * real part are added) until n_r real parts are sampled; the windows are runs
+ * of n_r,j consecutive sampled real parts (equal counts or Algorithm 1's
+ * n_r,j), shift at the middle of each run, request ceil(n_r,j inflate) +
+ * extra.  The plan becomes the context's windows and is written to
+ * sigma_out / n_req_out (host arrays of p, may be NULL); info may be NULL.
+ * The sampling solves replace the context's current pairs.  Errors:
+ * SWI_EINVAL, SWI_ESTATE (no potential/absorbers), SWI_ENOCONV (the sampling
+ * found too few pairs), SWI_ENOMEM, SWI_ECUDA. */
+swi_status swi_plan_windows_sampled(swi_ctx* ctx, int n_r, int p, const swi_plan_opts* opts,
+                                    double* sigma_out, int* n_req_out, swi_plan_info* info);
+
 /* Apply the shifted operator to a block: Y[:, c] = (A - sigma[c]) X[:, c] for
  * c < nvec; X and Y are complex128 [N][nvec] (Eq. 3's matrix-vector product,
  * the hot kernel of the Krylov loop).  sigma is a host array of nvec doubles.
@@ -207,6 +251,42 @@ swi_status swi_apply_c64(swi_ctx* ctx, int nvec, const float* sigma, const void*
  * Returns SWI_OK, or SWI_ENOCONV / SWI_HOLES with the merged pairs still
  * available (partial result); SWI_ESTATE if windows/potential are unset. */
 swi_status swi_solve(swi_ctx* ctx, const swi_solve_opts* opts, swi_solve_info* info);
+
+/* Continuation run (Section 2: a computed set of pairs is extended by adding
+ * windows while the old pairs are kept; the paper's Conclusions): solve the p
+ * new windows (sigma strictly increasing, n_req >= 1, host arrays) with the
+ * context's solver and opts, then pass their pairs and the context's current
+ * pairs through Algorithm 2 together -- each current pair belongs to the
+ * window of the last solve whose shift is nearest its real part (pairs set by
+ * swi_set_eigenpairs, e.g. restored from a checkpoint, form one window at the
+ * middle of their real parts) -- all windows in shift order, keeping
+ * opts->n_keep pairs (0: all) with U^T U = I.  With no current pairs it is a
+ * plain solve of the new windows.  Returns as swi_solve (SWI_HOLES when an
+ * interface of the union shows no redundancy); swi_get_windows then lists the
+ * union's windows.  Errors: SWI_EINVAL (windows, or more than 64 in all),
+ * SWI_ESTATE, SWI_ENOMEM, SWI_ECUDA. */
+swi_status swi_solve_more(swi_ctx* ctx, int p, const double* sigma, const int* n_req,
+                          const swi_solve_opts* opts, swi_solve_info* info);
+
+/* Automated hole filling (Algorithm 1's loop over holes): for every interface
+ * of the current windows that showed no redundancy in the last merge, a new
+ * window at the middle of the gap between the highest real part delivered by
+ * the lower window and the lowest delivered by the upper one, requesting
+ * n = max(1, ceil(3/2 gap / ((e_max - e_min)/N))) pairs (e_min, e_max: the
+ * extremal real parts of the spectrum, Algorithm 1's uniform-density scale);
+ * the new windows are solved as a continuation (swi_solve_more), repeated
+ * until no hole remains or max_rounds (0: 4) rounds ran.  *windows_added
+ * (may be NULL) counts the windows inserted.  Returns SWI_OK, SWI_HOLES
+ * (holes remain), SWI_ENOCONV, or the errors of swi_solve_more; SWI_ESTATE
+ * without a previous solve. */
+swi_status swi_fill_holes(swi_ctx* ctx, double e_min, double e_max, int max_rounds,
+                          const swi_solve_opts* opts, swi_solve_info* info, int* windows_added);
+
+/* Windows of the current pairs (shift order) and the interface flags of their
+ * last merge: sigma[j] (may be NULL), holes[j] = 1 when the interface between
+ * windows j and j + 1 showed no redundancy (0 for the last window); up to cap
+ * entries, the window count in *p. */
+swi_status swi_get_windows(swi_ctx* ctx, int cap, double* sigma, int* holes, int* p);
 
 /* Per-window outcome of the last solve: fills up to `cap` entries, returns the
  * window count in *p. */

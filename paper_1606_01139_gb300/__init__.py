@@ -25,8 +25,9 @@ PREC_F64, PREC_MIXED = 0, 1
 ARITH_DS, ARITH_F64 = 2, 1
 
 # Every entry point declared in include/swi.h.
-EXPORTS = ("swi_create", "swi_set_potential", "swi_set_absorber", "swi_set_windows", "swi_plan_windows",
-           "swi_apply", "swi_apply_ds", "swi_apply_c64", "swi_solve", "swi_refine", "swi_get_window_info", "swi_get_eigenpairs", "swi_copy_eigenpairs",
+EXPORTS = ("swi_create", "swi_set_potential", "swi_set_absorber", "swi_set_windows", "swi_plan_windows", "swi_plan_windows_sampled",
+           "swi_apply", "swi_apply_ds", "swi_apply_c64", "swi_solve", "swi_solve_more", "swi_fill_holes",
+           "swi_get_windows", "swi_refine", "swi_get_window_info", "swi_get_eigenpairs", "swi_copy_eigenpairs",
            "swi_set_eigenpairs", "swi_residuals", "swi_transmission", "swi_grad", "swi_profile",
            "swi_profile_read", "swi_transmission_noalloc", "swi_last_error", "swi_launch_count", "swi_destroy")
 
@@ -52,6 +53,20 @@ class RefineInfo(C.Structure):
     _fields_ = [("sweeps", C.c_int), ("n_pairs", C.c_int), ("n_converged", C.c_int), ("n_dropped", C.c_int),
                 ("matvecs", C.c_longlong), ("max_rel_res_in", C.c_double), ("max_rel_res", C.c_double),
                 ("t_s", C.c_double)]
+
+    def as_dict(self):
+        return {f[0]: getattr(self, f[0]) for f in self._fields_}
+
+
+class PlanOpts(C.Structure):
+    _fields_ = [("sample_req", C.c_int), ("max_samples", C.c_int), ("sample_tol", C.c_double),
+                ("inflate", C.c_double), ("extra", C.c_int), ("counts_rule", C.c_int),
+                ("max_matvecs", C.c_longlong)]
+
+
+class PlanInfo(C.Structure):
+    _fields_ = [("e_min", C.c_double), ("e_max", C.c_double), ("e_top", C.c_double), ("samples", C.c_int),
+                ("windows", C.c_int), ("matvecs", C.c_longlong), ("t_s", C.c_double)]
 
     def as_dict(self):
         return {f[0]: getattr(self, f[0]) for f in self._fields_}
@@ -90,10 +105,14 @@ def load(path: str = LIB_PATH):
         "swi_set_absorber": (I, [VP, VP, VP, I]),
         "swi_set_windows": (I, [VP, I, VP, VP]),
         "swi_plan_windows": (I, [VP, I, I, D, D, D, VP, VP]),
+        "swi_plan_windows_sampled": (I, [VP, I, I, P(PlanOpts), VP, VP, P(PlanInfo)]),
         "swi_apply": (I, [VP, I, VP, VP, VP, I]),
         "swi_apply_ds": (I, [VP, I, VP, VP, VP, I]),
         "swi_apply_c64": (I, [VP, I, VP, VP, VP, I]),
         "swi_solve": (I, [VP, P(SolveOpts), P(SolveInfo)]),
+        "swi_solve_more": (I, [VP, I, VP, VP, P(SolveOpts), P(SolveInfo)]),
+        "swi_fill_holes": (I, [VP, D, D, I, P(SolveOpts), P(SolveInfo), P(I)]),
+        "swi_get_windows": (I, [VP, I, VP, VP, P(I)]),
         "swi_refine": (I, [VP, P(RefineOpts), P(RefineInfo)]),
         "swi_get_window_info": (I, [VP, I, P(WindowInfo), P(I)]),
         "swi_get_eigenpairs": (I, [VP, P(I), P(VP), P(VP), P(I)]),
@@ -208,6 +227,18 @@ class Context:
                                                float(inflate), _ptr(s), _ptr(n)))
         return s, n
 
+    def plan_windows_sampled(self, n_r, p, sample_req=0, max_samples=0, sample_tol=0.0, inflate=0.0, extra=0,
+                             counts_rule=0, max_matvecs=0):
+        """Windows from extremal estimates and density sampling (Section 2.2.1); returns (sigma, n_req, info)."""
+        o = PlanOpts(sample_req=sample_req, max_samples=max_samples, sample_tol=sample_tol, inflate=inflate,
+                     extra=extra, counts_rule=counts_rule, max_matvecs=max_matvecs)
+        s = np.zeros(p)
+        n = np.zeros(p, dtype=np.int32)
+        info = PlanInfo()
+        self._check(self._lib.swi_plan_windows_sampled(self._h, int(n_r), int(p), C.byref(o), _ptr(s), _ptr(n),
+                                                       C.byref(info)))
+        return s[:info.windows], n[:info.windows], info.as_dict()
+
     # -- operator
     def apply(self, X, sigma):
         """(A - sigma_c) X[:, c] for X of shape (N, nvec) complex128 (numpy or torch CUDA)."""
@@ -254,8 +285,10 @@ class Context:
               seed=1, n_keep=0, arith=ARITH_DS, allow=(SWI_OK, SWI_ENOCONV, SWI_HOLES)):
         """Windowed solve; arith = ARITH_DS (double-single products, default) or ARITH_F64 (native).
 
-        block=1 runs single-vector windows (complex128 bases, double-single products); a
-        PREC_MIXED context always runs them, on complex64 bases (block must be 0 or 1)."""
+        block=1 runs single-vector windows (complex128 bases, double-single products), block=2
+        the same loop with two new vectors per window and step (both vectors of a doubly
+        degenerate eigenvalue); a PREC_MIXED context runs only these, on complex64 bases
+        (block 0, 1 or 2)."""
         o = SolveOpts(block=block, max_basis=max_basis, keep=keep, max_matvecs=max_matvecs, rel_tol=rel_tol,
                       eq_rtol=eq_rtol, drop_tol=drop_tol, seed=seed, n_keep=n_keep, arith=arith)
         info = SolveInfo()
@@ -263,6 +296,42 @@ class Context:
         d = info.as_dict()
         d["status"] = STATUS_NAMES[rc]
         return d
+
+    def solve_more(self, sigma, n_req, block=16, rel_tol=1e-10, max_basis=0, keep=0, max_matvecs=0, eq_rtol=0.0,
+                   drop_tol=0.0, seed=1, n_keep=0, arith=ARITH_DS, allow=(SWI_OK, SWI_ENOCONV, SWI_HOLES)):
+        """Continuation: solve new windows and merge them with the current pairs (Algorithm 2)."""
+        s, n = _c_arr(sigma, np.float64), _c_arr(n_req, np.int32)
+        o = SolveOpts(block=block, max_basis=max_basis, keep=keep, max_matvecs=max_matvecs, rel_tol=rel_tol,
+                      eq_rtol=eq_rtol, drop_tol=drop_tol, seed=seed, n_keep=n_keep, arith=arith)
+        info = SolveInfo()
+        rc = self._check(self._lib.swi_solve_more(self._h, len(s), _ptr(s), _ptr(n), C.byref(o), C.byref(info)), allow)
+        d = info.as_dict()
+        d["status"] = STATUS_NAMES[rc]
+        return d
+
+    def fill_holes(self, e_min, e_max, max_rounds=0, block=16, rel_tol=1e-10, max_basis=0, keep=0, max_matvecs=0,
+                   eq_rtol=0.0, drop_tol=0.0, seed=1, n_keep=0, arith=ARITH_DS,
+                   allow=(SWI_OK, SWI_ENOCONV, SWI_HOLES)):
+        """Algorithm 1's hole loop on the current windows; returns the info dict with "status", "windows_added"."""
+        o = SolveOpts(block=block, max_basis=max_basis, keep=keep, max_matvecs=max_matvecs, rel_tol=rel_tol,
+                      eq_rtol=eq_rtol, drop_tol=drop_tol, seed=seed, n_keep=n_keep, arith=arith)
+        info = SolveInfo()
+        added = C.c_int()
+        rc = self._check(self._lib.swi_fill_holes(self._h, float(e_min), float(e_max), int(max_rounds), C.byref(o),
+                                                  C.byref(info), C.byref(added)), allow)
+        d = info.as_dict()
+        d["status"] = STATUS_NAMES[rc]
+        d["windows_added"] = added.value
+        return d
+
+    def windows(self):
+        """(sigma[p], holes[p]) of the current pairs' windows (holes[j]: interface j, j + 1 without redundancy)."""
+        p = C.c_int()
+        self._check(self._lib.swi_get_windows(self._h, 0, None, None, C.byref(p)))
+        s = np.zeros(max(1, p.value))
+        h = np.zeros(max(1, p.value), dtype=np.int32)
+        self._check(self._lib.swi_get_windows(self._h, p.value, _ptr(s), _ptr(h), C.byref(p)))
+        return s[:p.value], h[:p.value]
 
     def window_info(self):
         p = C.c_int()

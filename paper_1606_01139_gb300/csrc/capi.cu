@@ -301,6 +301,20 @@ void merge_pairs(swi_ctx* c, const double2* Uin, int ldu, const std::vector<doub
 namespace {
 using namespace swi::host;
 
+}  // namespace
+
+void swi::host::record_windows(swi_ctx* c, const std::vector<double2>& eps_all, const std::vector<int>& win_of,
+                               int nwin) {
+  c->last_sigma = c->sigma;
+  c->last_eps_win = eps_all;
+  c->last_win_of = win_of;
+  c->last_holes.assign(std::max(0, nwin - 1), 0);
+  if (nwin > 1)
+    SWI_CUDA_TRY(cudaMemcpy(c->last_holes.data(), c->m_holes.p, sizeof(int) * (nwin - 1), cudaMemcpyDeviceToHost));
+}
+
+namespace {
+
 swi_status do_solve(swi_ctx* c, const swi_solve_opts* o, swi_solve_info* info) {
   if (!c->has_V || !c->has_G) return fail(c, SWI_ESTATE, "potential and absorbers must be set before solve");
   if (c->sigma.empty()) return fail(c, SWI_ESTATE, "windows must be set before solve");
@@ -651,6 +665,7 @@ swi_status do_solve(swi_ctx* c, const swi_solve_opts* o, swi_solve_info* info) {
   // ---- Algorithm 2 merge, selection, U^T U = I
   int minfo[4];
   merge_pairs(c, c->Uall.as<double2>(), n_all, eps_all, win_of, nwin, eq_rtol, drop_tol, opt.n_keep, minfo);
+  record_windows(c, eps_all, win_of, nwin);
   const int nout = minfo[0];
   c->Uall.release();
   // explicit FP64 residuals of the delivered pairs
@@ -1218,15 +1233,54 @@ swi_status swi_apply_c64(swi_ctx* c, int nvec, const float* sigma, const void* X
   });
 }
 
+// the solver of the context's precision and the options' block width
+static swi_status solve_dispatch(swi_ctx* c, const swi_solve_opts* opts, swi_solve_info* info) {
+  if (c->precision == SWI_PREC_MIXED) {
+    if (opts && opts->block > 2)
+      return fail(c, SWI_EINVAL, "SWI_PREC_MIXED runs windows of 1 or 2 vectors (block 0, 1 or 2)");
+    if (opts && opts->arith == SWI_ARITH_F64) return fail(c, SWI_EINVAL, "SWI_PREC_MIXED has no native-FP64 form");
+    return do_solve_sv(c, opts, info);
+  }
+  if (opts && (opts->block == 1 || opts->block == 2) && opts->arith != SWI_ARITH_F64) return do_solve_sv(c, opts, info);
+  return do_solve(c, opts, info);
+}
+
 swi_status swi_solve(swi_ctx* c, const swi_solve_opts* opts, swi_solve_info* info) {
+  return guarded(c, [&]() -> swi_status { return solve_dispatch(c, opts, info); });
+}
+
+swi_status swi_solve_more(swi_ctx* c, int p, const double* sigma, const int* n_req, const swi_solve_opts* opts,
+                          swi_solve_info* info) {
   return guarded(c, [&]() -> swi_status {
-    if (c->precision == SWI_PREC_MIXED) {
-      if (opts && opts->block > 1) return fail(c, SWI_EINVAL, "SWI_PREC_MIXED runs single-vector windows (block 0 or 1)");
-      if (opts && opts->arith == SWI_ARITH_F64) return fail(c, SWI_EINVAL, "SWI_PREC_MIXED has no native-FP64 form");
-      return do_solve_sv(c, opts, info);
+    if (!c->has_V || !c->has_G) return fail(c, SWI_ESTATE, "potential and absorbers must be set before solve");
+    return do_solve_more(c, p, sigma, n_req, opts, info, solve_dispatch);
+  });
+}
+
+swi_status swi_fill_holes(swi_ctx* c, double e_min, double e_max, int max_rounds, const swi_solve_opts* opts,
+                          swi_solve_info* info, int* windows_added) {
+  return guarded(c, [&]() -> swi_status {
+    if (windows_added) *windows_added = 0;
+    return do_fill_holes(c, e_min, e_max, max_rounds, opts, info, windows_added, solve_dispatch);
+  });
+}
+
+swi_status swi_plan_windows_sampled(swi_ctx* c, int n_r, int p, const swi_plan_opts* opts, double* sigma_out,
+                                    int* n_req_out, swi_plan_info* info) {
+  return guarded(c, [&]() -> swi_status {
+    return do_plan_sampled(c, n_r, p, opts, sigma_out, n_req_out, info, solve_dispatch);
+  });
+}
+
+swi_status swi_get_windows(swi_ctx* c, int cap, double* sigma, int* holes, int* p) {
+  return guarded(c, [&]() -> swi_status {
+    const int pw = (int)c->last_sigma.size();
+    if (p) *p = pw;
+    for (int j = 0; j < cap && j < pw; ++j) {
+      if (sigma) sigma[j] = c->last_sigma[j];
+      if (holes) holes[j] = j + 1 < pw && j < (int)c->last_holes.size() ? c->last_holes[j] : 0;
     }
-    if (opts && opts->block == 1 && opts->arith != SWI_ARITH_F64) return do_solve_sv(c, opts, info);
-    return do_solve(c, opts, info);
+    return SWI_OK;
   });
 }
 
@@ -1274,6 +1328,10 @@ swi_status swi_set_eigenpairs(swi_ctx* c, int n, const void* eps, const void* U,
     c->npairs = n;
     c->have_RL = false;
     c->resid.clear();
+    c->last_sigma.clear();  // restored pairs carry no window records
+    c->last_eps_win.clear();
+    c->last_win_of.clear();
+    c->last_holes.clear();
     return SWI_OK;
   });
 }

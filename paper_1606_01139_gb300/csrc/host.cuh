@@ -81,6 +81,13 @@ struct swi_ctx {
   double maxabsV = 0.0, maxG = 0.0;
   std::vector<double> sigma;
   std::vector<int> nreq;
+  // windows of the current pairs: shifts (shift order), the eigenvalues each
+  // window delivered before the merge, and the merge's interface flags
+  // (1 = no redundancy across the interface: a presumed hole)
+  std::vector<double> last_sigma;
+  std::vector<double2> last_eps_win;
+  std::vector<int> last_win_of;
+  std::vector<int> last_holes;
   // current pairs
   int npairs = 0;
   DevMem eps, U;  // [n], [N][n]
@@ -144,6 +151,17 @@ void sync(cudaStream_t s);
 void apply_block(swi_ctx* c, const double2* X, int ldx, double2* Y, int ldy, int ncols, bool ds = false);
 void explicit_residuals(swi_ctx* c, const double2* Ud, int ldu, const double2* epsd, int n, std::vector<double>& out);
 void gram_work_ensure(swi_ctx* c, size_t elems);
+// after a solve's merge: remember its windows, their delivered eigenvalues and
+// the interface flags (read from the merge's device array)
+void record_windows(swi_ctx* c, const std::vector<double2>& eps_all, const std::vector<int>& win_of, int nwin);
+// continuation and hole filling (windows.cu); solve is the context's solver
+swi_status do_solve_more(swi_ctx* c, int p, const double* sigma, const int* n_req, const swi_solve_opts* o,
+                         swi_solve_info* info, swi_status (*solve)(swi_ctx*, const swi_solve_opts*, swi_solve_info*));
+swi_status do_fill_holes(swi_ctx* c, double e_min, double e_max, int max_rounds, const swi_solve_opts* o,
+                         swi_solve_info* info, int* windows_added,
+                         swi_status (*solve)(swi_ctx*, const swi_solve_opts*, swi_solve_info*));
+swi_status do_plan_sampled(swi_ctx* c, int n_r, int p, const swi_plan_opts* po, double* sigma_out, int* n_req_out,
+                           swi_plan_info* pinfo, swi_status (*solve)(swi_ctx*, const swi_solve_opts*, swi_solve_info*));
 // the windowed solve with single-vector windows (solve_sv.cu): block width 1
 // in an FP64 context, and every solve of a SWI_PREC_MIXED context
 swi_status do_solve_sv(swi_ctx* c, const swi_solve_opts* o, swi_solve_info* info);

@@ -1,6 +1,8 @@
 // Gram-Schmidt passes of the single-vector Krylov loop (Section 2.1: one new
 // vector per window and step, as in the implicitly restarted Arnoldi method the
-// paper runs), batched over the windows of one solve.
+// paper runs), batched over the windows of one solve; the same passes serve
+// windows that add a block of nb = 2 vectors per step (a template parameter:
+// each pass still streams the basis once, for both new vectors).
 //
 // Every window keeps its basis row-major, Q [N][ld] (a grid point's basis
 // coefficients are contiguous), so each pass of classical Gram-Schmidt against
@@ -12,12 +14,13 @@
 //    tails (FMA), sums TwoSum-compensated, ~2^-46 relative per term (GB300's
 //    FP64 rate would cap these passes near a third of the HBM bandwidth).
 //
-//  sv_gram_kernel:   part[chunk][i] = sum_{rows of chunk} conj(Q[r, i]) w[r]
+//  sv_gram_kernel:   part[chunk][i][b] = sum_{rows of chunk} conj(Q[r, i]) w[r, b]
 //                    (a block per 32-column slab and row chunk, one column per lane)
-//  sv_update_kernel: w[r] -= Q[r, :] c (a warp per row), then either the next
+//  sv_update_kernel: w[r, :] -= Q[r, :] c (a warp per row), then either the next
 //                    Gram's partials (FUSE_GRAM, the row's values reused from
-//                    registers: one read of Q for both passes) or ||w||^2
-//  sv_reduce_kernel: FP64 sums of the chunk partials, added into a column of H
+//                    registers: one read of Q for both passes) or w^H w
+//  sv_reduce_kernel: FP64 sums of the chunk partials, added into columns of H;
+//                    for w^H w the Cholesky factor of the block (Cholesky-QR)
 // Chunks hold at most 1024 rows: the per-lane FP32 (or double-single) partial
 // sums stay short, chunks are combined in FP64.
 #include <algorithm>
@@ -36,6 +39,13 @@ constexpr int kWarps = kThreads / 32;
 struct PolC64 {
   using T = float2;   // basis element
   using A = float2;   // accumulator
+  using S = float2;   // an element prepared for products (no split in FP32)
+  __device__ static S split(T v) { return v; }
+  __device__ static S bcast0(S v) {
+    return make_float2(__shfl_sync(0xffffffffu, v.x, 0), __shfl_sync(0xffffffffu, v.y, 0));
+  }
+  __device__ static void conj_mac_s(A& a, S q, S w) { conj_mac(a, q, w); }
+  __device__ static void mac_s(A& a, S q, S c) { mac(a, q, c); }
   __device__ static A zero() { return make_float2(0.f, 0.f); }
   // a += conj(q) * w
   __device__ static void conj_mac(A& a, T q, T w) {
@@ -54,37 +64,62 @@ struct PolC64 {
   __device__ static double2 to_d(A a) { return make_double2(a.x, a.y); }
   __device__ static T sub(T w, A d) { return make_float2(w.x - d.x, w.y - d.y); }
   __device__ static T from_c(double2 c) { return make_float2((float)c.x, (float)c.y); }
-  __device__ static double abs2(T w) { return (double)w.x * w.x + (double)w.y * w.y; }
 };
+
+// x = hi + lo from the bit fields alone (integer and FP32 pipes only): hi is x
+// rounded to 24 significant bits, lo the remainder rounded to a float.  Values
+// below 2^-74 split to (0, 0) and magnitudes are capped at 2^126: the basis
+// entries, new vectors and coefficients of the loop lie far inside that range,
+// and no FP64 instruction is issued (a predicated FP64 fallback would occupy
+// GB300's narrow FP64 pipe on every element).
+__device__ __forceinline__ void split_fast(double x, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned int top = (unsigned int)(b >> 32);
+  const unsigned int sgn = top & 0x80000000u;
+  const int e0 = (int)((top >> 20) & 0x7ff);
+  const bool small = e0 < 949;
+  const int e = min(max(e0, 949), 1149);
+  const unsigned int up = (unsigned int)(b >> 28) & 1u;
+  const unsigned int fb = ((unsigned int)(e - 896) << 23 | ((unsigned int)(b >> 29) & 0x7fffffu)) + up;
+  const int rem = (int)((unsigned int)b & 0x1fffffffu) - (int)(up << 29);
+  const float t = (float)rem * __uint_as_float((unsigned int)(e - 948) << 23);
+  hi = small ? 0.f : __uint_as_float(sgn | fb);
+  lo = small ? 0.f : (sgn ? -t : t);
+}
 
 struct PolDs {
   using T = double2;
   struct A {
     float rh, re, ih, ie;
   };
+  struct S {  // heads and tails of the real and imaginary parts
+    float rh, rl, ih, il;
+  };
+  __device__ static S split(T v) {
+    S o;
+    split_fast(v.x, o.rh, o.rl);
+    split_fast(v.y, o.ih, o.il);
+    return o;
+  }
+  __device__ static S bcast0(S v) {
+    return S{__shfl_sync(0xffffffffu, v.rh, 0), __shfl_sync(0xffffffffu, v.rl, 0), __shfl_sync(0xffffffffu, v.ih, 0),
+             __shfl_sync(0xffffffffu, v.il, 0)};
+  }
+  // a += conj(q) * w
+  __device__ static void conj_mac_s(A& a, const S& q, const S& w) {
+    ds::fma_acc(a.rh, a.re, q.rh, q.rl, w.rh, w.rl);
+    ds::fma_acc(a.rh, a.re, q.ih, q.il, w.ih, w.il);
+    ds::fma_acc(a.ih, a.ie, q.rh, q.rl, w.ih, w.il);
+    ds::fma_acc(a.ih, a.ie, -q.ih, -q.il, w.rh, w.rl);
+  }
+  // a += q * c
+  __device__ static void mac_s(A& a, const S& q, const S& c) {
+    ds::fma_acc(a.rh, a.re, q.rh, q.rl, c.rh, c.rl);
+    ds::fma_acc(a.rh, a.re, -q.ih, -q.il, c.ih, c.il);
+    ds::fma_acc(a.ih, a.ie, q.rh, q.rl, c.ih, c.il);
+    ds::fma_acc(a.ih, a.ie, q.ih, q.il, c.rh, c.rl);
+  }
   __device__ static A zero() { return A{0.f, 0.f, 0.f, 0.f}; }
-  __device__ static void conj_mac(A& a, T q, T w) {
-    float qrh, qrl, qih, qil, wrh, wrl, wih, wil;
-    ds::split_bits(q.x, qrh, qrl);
-    ds::split_bits(q.y, qih, qil);
-    ds::split_bits(w.x, wrh, wrl);
-    ds::split_bits(w.y, wih, wil);
-    ds::fma_acc(a.rh, a.re, qrh, qrl, wrh, wrl);
-    ds::fma_acc(a.rh, a.re, qih, qil, wih, wil);
-    ds::fma_acc(a.ih, a.ie, qrh, qrl, wih, wil);
-    ds::fma_acc(a.ih, a.ie, -qih, -qil, wrh, wrl);
-  }
-  __device__ static void mac(A& a, T q, T c) {
-    float qrh, qrl, qih, qil, crh, crl, cih, cil;
-    ds::split_bits(q.x, qrh, qrl);
-    ds::split_bits(q.y, qih, qil);
-    ds::split_bits(c.x, crh, crl);
-    ds::split_bits(c.y, cih, cil);
-    ds::fma_acc(a.rh, a.re, qrh, qrl, crh, crl);
-    ds::fma_acc(a.rh, a.re, -qih, -qil, cih, cil);
-    ds::fma_acc(a.ih, a.ie, qrh, qrl, cih, cil);
-    ds::fma_acc(a.ih, a.ie, qih, qil, crh, crl);
-  }
   __device__ static A add(A a, A b) {
     const ds::df r = ds::two_sum(a.rh, b.rh);
     const ds::df i = ds::two_sum(a.ih, b.ih);
@@ -100,11 +135,10 @@ struct PolDs {
     return make_double2(w.x - dd.x, w.y - dd.y);
   }
   __device__ static T from_c(double2 c) { return c; }
-  __device__ static double abs2(T w) { return fma(w.x, w.x, w.y * w.y); }
 };
 
 // ----------------------------------------------------------------- Gram pass
-template <class Pol>
+template <class Pol, int NB>
 __global__ void __launch_bounds__(kThreads) sv_gram_kernel(const __grid_constant__ SvBatch batch, int N, int rpc) {
   using T = typename Pol::T;
   using A = typename Pol::A;
@@ -116,181 +150,339 @@ __global__ void __launch_bounds__(kThreads) sv_gram_kernel(const __grid_constant
   const T* __restrict__ w = static_cast<const T*>(J.w);
   const int r0 = blockIdx.x * rpc, r1 = min(N, r0 + rpc);
   const bool on = col < J.ncols;
-  // two interleaved accumulators per lane for instruction-level parallelism
-  A a0 = Pol::zero(), a1 = Pol::zero();
+  // two interleaved accumulators per lane and column of w (instruction-level parallelism)
+  A a0[NB], a1[NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) a0[b] = a1[b] = Pol::zero();
   int r = r0 + warp;
   for (; r + kWarps < r1; r += 2 * kWarps) {
     const T q0 = on ? __ldg(Q + (long long)r * J.ldq + col) : T{};
     const T q1 = on ? __ldg(Q + (long long)(r + kWarps) * J.ldq + col) : T{};
-    const T w0 = w[(long long)r * J.ldw], w1 = w[(long long)(r + kWarps) * J.ldw];
-    Pol::conj_mac(a0, q0, w0);
-    Pol::conj_mac(a1, q1, w1);
+    const auto s0 = Pol::split(q0), s1 = Pol::split(q1);
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      Pol::conj_mac_s(a0[b], s0, Pol::split(w[(long long)r * J.ldw + b]));
+      Pol::conj_mac_s(a1[b], s1, Pol::split(w[(long long)(r + kWarps) * J.ldw + b]));
+    }
   }
   if (r < r1) {
-    const T q0 = on ? __ldg(Q + (long long)r * J.ldq + col) : T{};
-    Pol::conj_mac(a0, q0, w[(long long)r * J.ldw]);
+    const auto s0 = Pol::split(on ? __ldg(Q + (long long)r * J.ldq + col) : T{});
+#pragma unroll
+    for (int b = 0; b < NB; ++b) Pol::conj_mac_s(a0[b], s0, Pol::split(w[(long long)r * J.ldw + b]));
   }
-  __shared__ double2 red[kWarps][32];
-  red[warp][lane] = Pol::to_d(Pol::add(a0, a1));
+  __shared__ double2 red[kWarps][NB][32];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) red[warp][b][lane] = Pol::to_d(Pol::add(a0[b], a1[b]));
   __syncthreads();
   if (warp == 0 && on) {
-    double2 s = make_double2(0.0, 0.0);
 #pragma unroll
-    for (int k = 0; k < kWarps; ++k) {
-      s.x += red[k][lane].x;
-      s.y += red[k][lane].y;
+    for (int b = 0; b < NB; ++b) {
+      double2 s = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int k = 0; k < kWarps; ++k) {
+        s.x += red[k][b][lane].x;
+        s.y += red[k][b][lane].y;
+      }
+      J.part[(long long)blockIdx.x * J.ldp + col * NB + b] = s;
     }
-    J.part[(long long)blockIdx.x * J.ldp + col] = s;
   }
 }
 
-// ----------------------------------------------------------------- update pass (+ Gram or norm)
-// A warp per row; lane l holds columns l, l + 32, ... (NT of them, the row's
-// values kept in registers for the fused Gram).
-template <class Pol, int NT, bool FUSE_GRAM>
+// ----------------------------------------------------------------- update pass (+ Gram or w^H w)
+// A warp per row; lane l holds basis columns l, l + 32, ... (NT of them, the
+// row's values kept in registers for the fused Gram).
+template <class Pol, int NT, int NB, bool FUSE_GRAM>
 __global__ void __launch_bounds__(kThreads) sv_update_kernel(const __grid_constant__ SvBatch batch, int N, int rpc) {
   using T = typename Pol::T;
   using A = typename Pol::A;
-  extern __shared__ double2 sh[];  // Gram partials [kWarps][ncols], then the coefficients c [ncols]
+  using Sp = typename Pol::S;
+  // shared: the coefficients c in split form ([ncols][NB], 16-byte slots),
+  // then the cross-warp partials
+  extern __shared__ double2 sh[];
   const SvJob& J = batch.job[blockIdx.y];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int ncols = J.ncols;
-  double2* red = sh;
-  T* cs = reinterpret_cast<T*>(sh + (FUSE_GRAM ? kWarps * ncols : kWarps));
-  for (int i = threadIdx.x; i < ncols; i += kThreads) cs[i] = Pol::from_c(J.c[i]);
+  Sp* cs = reinterpret_cast<Sp*>(sh);
+  double2* red = sh + (size_t)ncols * NB;
+  for (int i = threadIdx.x; i < ncols * NB; i += kThreads) cs[i] = Pol::split(Pol::from_c(J.c[i]));
   __syncthreads();
   const T* __restrict__ Q = static_cast<const T*>(J.Q);
   T* w = static_cast<T*>(J.w);
   const int r0 = blockIdx.x * rpc, r1 = min(N, r0 + rpc);
-  A acc[FUSE_GRAM ? NT : 1];
+  constexpr int NA = FUSE_GRAM ? NT : 1;
+  A acc[NA][NB];
 #pragma unroll
-  for (int t = 0; t < (FUSE_GRAM ? NT : 1); ++t) acc[t] = Pol::zero();
-  double nrm = 0.0;
+  for (int t = 0; t < NA; ++t)
+#pragma unroll
+    for (int b = 0; b < NB; ++b) acc[t][b] = Pol::zero();
+  double2 g[NB * NB];  // lane 0: w^H w of its rows (FP64)
+#pragma unroll
+  for (int e = 0; e < NB * NB; ++e) g[e] = make_double2(0.0, 0.0);
   for (int r = r0 + warp; r < r1; r += kWarps) {
-    T q[NT];
+    Sp q[NT];
 #pragma unroll
     for (int t = 0; t < NT; ++t) {
       const int i = lane + 32 * t;
-      q[t] = i < ncols ? __ldg(Q + (long long)r * J.ldq + i) : T{};
+      q[t] = Pol::split(i < ncols ? __ldg(Q + (long long)r * J.ldq + i) : T{});
     }
-    A d = Pol::zero();
+    A d[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) d[b] = Pol::zero();
 #pragma unroll
     for (int t = 0; t < NT; ++t) {
       const int i = lane + 32 * t;
-      if (i < ncols) Pol::mac(d, q[t], cs[i]);
+      if (i < ncols)
+#pragma unroll
+        for (int b = 0; b < NB; ++b) Pol::mac_s(d[b], q[t], cs[i * NB + b]);
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) d = Pol::add(d, Pol::shfl_xor(d, o));
-    const T wv = Pol::sub(w[(long long)r * J.ldw], d);
-    if (lane == 0) w[(long long)r * J.ldw] = wv;
+    for (int b = 0; b < NB; ++b)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) d[b] = Pol::add(d[b], Pol::shfl_xor(d[b], o));
+    // the row's new values are formed by lane 0 alone (in the complex128 form
+    // that takes FP64 instructions, kept off the other 31 lanes) and their
+    // split forms broadcast
+    Sp ws[NB]{};
+    if (lane == 0) {
+      T wv[NB];
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        wv[b] = Pol::sub(w[(long long)r * J.ldw + b], d[b]);
+        w[(long long)r * J.ldw + b] = wv[b];
+        if (FUSE_GRAM) ws[b] = Pol::split(wv[b]);
+      }
+      if (!FUSE_GRAM) {
+#pragma unroll
+        for (int a = 0; a < NB; ++a)
+#pragma unroll
+          for (int b = 0; b < NB; ++b) {
+            const double ar = wv[a].x, ai = wv[a].y, br = wv[b].x, bi = wv[b].y;
+            g[a * NB + b].x += ar * br + ai * bi;
+            g[a * NB + b].y += ar * bi - ai * br;
+          }
+      }
+    }
     if (FUSE_GRAM) {
 #pragma unroll
-      for (int t = 0; t < NT; ++t) Pol::conj_mac(acc[FUSE_GRAM ? t : 0], q[t], wv);
-    } else {
-      nrm += Pol::abs2(wv);
+      for (int b = 0; b < NB; ++b) ws[b] = Pol::bcast0(ws[b]);
+#pragma unroll
+      for (int t = 0; t < NT; ++t)
+#pragma unroll
+        for (int b = 0; b < NB; ++b) Pol::conj_mac_s(acc[FUSE_GRAM ? t : 0][b], q[t], ws[b]);
     }
   }
   double2* out = J.part + (long long)blockIdx.x * J.ldp;
   if (!FUSE_GRAM) {
-    if (lane == 0) red[warp] = make_double2(nrm, 0.0);
+    if (lane == 0)
+#pragma unroll
+      for (int e = 0; e < NB * NB; ++e) red[warp * NB * NB + e] = g[e];  // lane 0 holds its warp's rows
     __syncthreads();
-    if (threadIdx.x == 0) {
-      double s = 0.0;
-      for (int k = 0; k < kWarps; ++k) s += red[k].x;
-      out[0] = make_double2(s, 0.0);
+    if (threadIdx.x < NB * NB) {
+      double2 s = make_double2(0.0, 0.0);
+      for (int k = 0; k < kWarps; ++k) {
+        s.x += red[k * NB * NB + threadIdx.x].x;
+        s.y += red[k * NB * NB + threadIdx.x].y;
+      }
+      out[threadIdx.x] = s;
     }
     return;
   }
+  // cross-warp sums, one 32-column slab at a time: red [kWarps][NB][32]
 #pragma unroll
   for (int t = 0; t < NT; ++t) {
-    const int i = lane + 32 * t;
-    if (i < ncols) red[warp * ncols + i] = Pol::to_d(acc[FUSE_GRAM ? t : 0]);
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < ncols; i += kThreads) {
-    double2 s = make_double2(0.0, 0.0);
-    for (int k = 0; k < kWarps; ++k) {
-      s.x += red[k * ncols + i].x;
-      s.y += red[k * ncols + i].y;
+    if (32 * t >= ncols) break;  // uniform over the block
+#pragma unroll
+    for (int b = 0; b < NB; ++b) red[(warp * NB + b) * 32 + lane] = Pol::to_d(acc[FUSE_GRAM ? t : 0][b]);
+    __syncthreads();
+    if (threadIdx.x < 32 * NB) {
+      const int b = threadIdx.x >> 5, l = threadIdx.x & 31, i = l + 32 * t;
+      if (i < ncols) {
+        double2 s = make_double2(0.0, 0.0);
+        for (int k = 0; k < kWarps; ++k) {
+          s.x += red[(k * NB + b) * 32 + l].x;
+          s.y += red[(k * NB + b) * 32 + l].y;
+        }
+        out[i * NB + b] = s;
+      }
     }
-    out[i] = s;
+    __syncthreads();
   }
 }
 
 // ----------------------------------------------------------------- chunk reduction
-// A block per 32 columns and job; 8 lanes per column step through the chunks
+// A block per 32 entries and job; 32 lanes per entry step through the chunks
 // (independent loads in flight), then combine in shared memory.
-__global__ void sv_reduce_kernel(const __grid_constant__ SvReduceBatch batch) {
+constexpr int kRedLanes = 32;
+
+// upper Cholesky factor R of the Hermitian nb x nb matrix G (G = R^H R), its
+// inverse, and whether a pivot fell below 1e-14 of its diagonal entry
+__device__ bool chol_small(const double2* G, int nb, double2* R, double2* Ri) {
+  bool bad = false;
+  for (int e = 0; e < 4; ++e) R[e] = Ri[e] = make_double2(0.0, 0.0);
+  const double g00 = G[0].x;
+  if (!(g00 > 0.0)) return true;
+  const double r00 = sqrt(g00);
+  R[0] = make_double2(r00, 0.0);
+  Ri[0] = make_double2(1.0 / r00, 0.0);
+  if (nb == 1) return false;
+  const double2 r01 = make_double2(G[1].x / r00, G[1].y / r00);
+  const double d = G[3].x - (r01.x * r01.x + r01.y * r01.y);
+  if (!(d > 1e-14 * G[3].x)) {
+    bad = true;
+  }
+  const double r11 = d > 0.0 ? sqrt(d) : 0.0;
+  R[1] = r01;
+  R[3] = make_double2(r11, 0.0);
+  if (r11 > 0.0) {
+    Ri[1] = make_double2(-r01.x / (r00 * r11), -r01.y / (r00 * r11));
+    Ri[3] = make_double2(1.0 / r11, 0.0);
+  }
+  return bad;
+}
+
+__global__ void __launch_bounds__(32 * kRedLanes) sv_reduce_kernel(const __grid_constant__ SvReduceBatch batch) {
   const SvReduceJob& J = batch.job[blockIdx.y];
   const int cl = threadIdx.x & 31, k = threadIdx.x >> 5;
   const int i = blockIdx.x * 32 + cl;
-  const int ncols = J.mode == 1 ? 1 : J.ncols;
-  if (blockIdx.x * 32 >= ncols) return;
-  double2 a = make_double2(0.0, 0.0);
-  if (i < ncols)
-    for (int ch = k; ch < J.nchunks; ch += 8) {
-      const double2 v = J.part[(long long)ch * J.ldp + i];
-      a.x += v.x;
-      a.y += v.y;
+  const int nent = J.mode == 0 ? J.ncols * J.nb : J.nb * J.nb;
+  if (blockIdx.x * 32 >= nent) return;  // uniform over the block
+  double2 a0 = make_double2(0.0, 0.0), a1 = a0;
+  if (i < nent) {
+    int ch = k;
+    for (; ch + kRedLanes < J.nchunks; ch += 2 * kRedLanes) {
+      const double2 v0 = J.part[(long long)ch * J.ldp + i];
+      const double2 v1 = J.part[(long long)(ch + kRedLanes) * J.ldp + i];
+      a0.x += v0.x;
+      a0.y += v0.y;
+      a1.x += v1.x;
+      a1.y += v1.y;
     }
-  __shared__ double2 red[8][32];
-  red[k][cl] = a;
+    if (ch < J.nchunks) {
+      const double2 v0 = J.part[(long long)ch * J.ldp + i];
+      a0.x += v0.x;
+      a0.y += v0.y;
+    }
+  }
+  __shared__ double2 red[kRedLanes][32];
+  __shared__ double2 fin[4];
+  red[k][cl] = make_double2(a0.x + a1.x, a0.y + a1.y);
   __syncthreads();
-  if (k != 0 || i >= ncols) return;
-  double2 s = make_double2(0.0, 0.0);
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    s.x += red[q][cl].x;
-    s.y += red[q][cl].y;
+  if (k == 0 && i < nent) {
+    double2 s = make_double2(0.0, 0.0);
+#pragma unroll 8
+    for (int q = 0; q < kRedLanes; ++q) {
+      s.x += red[q][cl].x;
+      s.y += red[q][cl].y;
+    }
+    if (J.mode == 0) {
+      if (J.C) J.C[i] = s;
+      if (J.H) {
+        double2* h = J.H + (long long)(i / J.nb) * J.ldh + i % J.nb;
+        *h = make_double2(h->x + s.x, h->y + s.y);
+      }
+    } else {
+      fin[i] = s;
+    }
   }
+  if (J.mode == 0) return;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double2 R[4], Ri[4];
+  const bool bad = chol_small(fin, J.nb, R, Ri);
+  const int nb = J.nb;
   if (J.mode == 1) {
-    const double beta = sqrt(s.x);
-    if (J.H) J.H[0] = make_double2(beta, 0.0);
-    if (J.invb) *J.invb = beta > 0.0 ? 1.0 / beta : 0.0;
-    return;
+    for (int e = 0; e < nb * nb; ++e) {
+      J.r[e] = Ri[e];
+      J.r[4 + e] = R[e];
+    }
+    if (nb == 1 && J.H) J.H[0] = R[0];
+  } else {
+    // R = R2 R1 (both upper triangular, nb = 2)
+    const double2* R1 = J.r + 4;
+    for (int e = 0; e < 4; ++e) J.r[e] = Ri[e];
+    if (J.H) {
+      for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+          double2 s = make_double2(0.0, 0.0);
+          for (int q = 0; q < 2; ++q) {
+            const double2 x = R[a * 2 + q], y = R1[q * 2 + b];
+            s.x += x.x * y.x - x.y * y.y;
+            s.y += x.x * y.y + x.y * y.x;
+          }
+          J.H[(long long)a * J.ldh + b] = s;
+        }
+    }
   }
-  if (J.C) J.C[i] = s;
-  if (J.H) {
-    double2* h = J.H + (long long)i * J.ldh;
-    *h = make_double2(h->x + s.x, h->y + s.y);
-  }
+  if (bad) J.r[8] = make_double2(1.0, 0.0);
 }
 
 // ----------------------------------------------------------------- normalisation
-template <class T>
+template <class T, int NB>
 __global__ void sv_normalize_kernel(const __grid_constant__ SvNormBatch batch, int N) {
   const SvNormJob& J = batch.job[blockIdx.y];
-  const double s = *J.invb;
+  double2 r[NB * NB];
+#pragma unroll
+  for (int e = 0; e < NB * NB; ++e) r[e] = J.r[e];
   const T* w = static_cast<const T*>(J.w);
   T* d1 = static_cast<T*>(J.dst1);
   T* d2 = static_cast<T*>(J.dst2);
-  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < N; r += (long long)gridDim.x * blockDim.x) {
-    const T v = w[r * J.ldw];
-    T o;
-    o.x = (decltype(v.x))(v.x * s);
-    o.y = (decltype(v.y))(v.y * s);
-    d1[r * J.ld1] = o;
-    if (d2) d2[r * J.ld2] = o;
+  for (long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x; row < N;
+       row += (long long)gridDim.x * blockDim.x) {
+    double2 v[NB];
+#pragma unroll
+    for (int a = 0; a < NB; ++a) {
+      const T x = w[row * J.ldw + a];
+      v[a] = make_double2((double)x.x, (double)x.y);
+    }
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      double re = 0.0, im = 0.0;
+#pragma unroll
+      for (int a = 0; a < NB; ++a) {
+        re += v[a].x * r[a * NB + b].x - v[a].y * r[a * NB + b].y;
+        im += v[a].x * r[a * NB + b].y + v[a].y * r[a * NB + b].x;
+      }
+      T o;
+      o.x = (decltype(o.x))re;
+      o.y = (decltype(o.y))im;
+      d1[row * J.ld1 + b] = o;
+      if (d2) d2[row * J.ld2 + b] = o;
+    }
   }
 }
 
-template <class Pol, int NT, bool FUSE>
+template <class Pol, int NT, int NB, bool FUSE>
 void launch_update_nt(const SvBatch& b, int N, int rpc, int maxcols, cudaStream_t s) {
   const int nchunks = (N + rpc - 1) / rpc;
-  const size_t smem = sizeof(double2) * ((FUSE ? (size_t)kWarps * maxcols : kWarps) + maxcols);
+  const size_t smem = sizeof(double2) * ((size_t)maxcols * NB + (FUSE ? (size_t)kWarps * NB * 32 : kWarps * NB * NB));
   if (smem > 48 * 1024)
-    SWI_CUDA_TRY(cudaFuncSetAttribute(sv_update_kernel<Pol, NT, FUSE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
-  sv_update_kernel<Pol, NT, FUSE><<<dim3(nchunks, b.n), kThreads, smem, s>>>(b, N, rpc);
+    SWI_CUDA_TRY(cudaFuncSetAttribute(sv_update_kernel<Pol, NT, NB, FUSE>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  sv_update_kernel<Pol, NT, NB, FUSE><<<dim3(nchunks, b.n), kThreads, smem, s>>>(b, N, rpc);
 }
 
-template <class Pol, bool FUSE>
+template <class Pol, int NB, bool FUSE>
 void launch_update(const SvBatch& b, int N, int rpc, int maxcols, cudaStream_t s) {
-  if (maxcols <= 64) launch_update_nt<Pol, 2, FUSE>(b, N, rpc, maxcols, s);
-  else if (maxcols <= 128) launch_update_nt<Pol, 4, FUSE>(b, N, rpc, maxcols, s);
-  else if (maxcols <= 256) launch_update_nt<Pol, 8, FUSE>(b, N, rpc, maxcols, s);
-  else if (maxcols <= 512) launch_update_nt<Pol, 16, FUSE>(b, N, rpc, maxcols, s);
-  else launch_update_nt<Pol, 32, FUSE>(b, N, rpc, maxcols, s);
+  if (maxcols <= 64) launch_update_nt<Pol, 2, NB, FUSE>(b, N, rpc, maxcols, s);
+  else if (maxcols <= 128) launch_update_nt<Pol, 4, NB, FUSE>(b, N, rpc, maxcols, s);
+  else if (maxcols <= 256) launch_update_nt<Pol, 8, NB, FUSE>(b, N, rpc, maxcols, s);
+  else if (maxcols <= 384) launch_update_nt<Pol, 12, NB, FUSE>(b, N, rpc, maxcols, s);
+  else if (maxcols <= 512) launch_update_nt<Pol, 16, NB, FUSE>(b, N, rpc, maxcols, s);
+  else if constexpr (NB == 1) launch_update_nt<Pol, 32, NB, FUSE>(b, N, rpc, maxcols, s);
+  else throw Error{SWI_EINVAL, "Gram-Schmidt pass: at most 512 basis columns with 2-vector blocks"};
+}
+
+template <class Pol, int NB>
+void launch_pass_nb(const SvBatch& b, int mode, int N, int rpc, int maxcols, cudaStream_t s) {
+  const int nchunks = (N + rpc - 1) / rpc;
+  if (mode == SV_GRAM) {
+    const dim3 grid(nchunks, (maxcols + 31) / 32, b.n);
+    sv_gram_kernel<Pol, NB><<<grid, kThreads, 0, s>>>(b, N, rpc);
+  } else if (mode == SV_UPDATE_GRAM) {
+    launch_update<Pol, NB, true>(b, N, rpc, maxcols, s);
+  } else {
+    launch_update<Pol, NB, false>(b, N, rpc, maxcols, s);
+  }
 }
 
 }  // namespace
@@ -300,29 +492,28 @@ int sv_rows_per_chunk(int N, int njobs) {
   // 1024 rows per chunk (the bound on the per-lane partial sums)
   const long long target = 8LL * 152;
   long long per = (long long)N * std::max(njobs, 1) / target;
-  per = std::max<long long>(64, std::min<long long>(1024, per));
+  per = std::max<long long>(256, std::min<long long>(1024, per));
   return (int)((per + 7) / 8 * 8);
 }
 
-void launch_sv_pass(const SvBatch& b, int mode, bool ds, int N, int rpc, cudaStream_t s, long long* launches) {
+void launch_sv_pass(const SvBatch& b, int mode, bool ds, int nb, int N, int rpc, cudaStream_t s,
+                    long long* launches) {
   if (b.n <= 0) return;
+  if (nb != 1 && nb != 2) throw Error{SWI_EINVAL, "Gram-Schmidt pass: blocks of 1 or 2 vectors"};
   int maxcols = 0;
   for (int q = 0; q < b.n; ++q) {
-    if (b.job[q].ncols > 1024 || b.job[q].ncols < 1) throw Error{SWI_EINVAL, "Gram-Schmidt pass: 1..1024 columns"};
-    maxcols = std::max(maxcols, b.job[q].ncols);
+    const int nc = b.job[q].ncols;
+    if (nc > 1024 || nc < 0 || (nc == 0 && mode != SV_UPDATE_NORM))
+      throw Error{SWI_EINVAL, "Gram-Schmidt pass: 1..1024 basis columns (0 only for w^H w)"};
+    maxcols = std::max(maxcols, nc);
   }
   if (rpc < 8 || rpc > 1024) throw Error{SWI_EINVAL, "Gram-Schmidt pass: rows per chunk out of range"};
-  const int nchunks = (N + rpc - 1) / rpc;
-  if (mode == SV_GRAM) {
-    const dim3 grid(nchunks, (maxcols + 31) / 32, b.n);
-    if (ds) sv_gram_kernel<PolDs><<<grid, kThreads, 0, s>>>(b, N, rpc);
-    else sv_gram_kernel<PolC64><<<grid, kThreads, 0, s>>>(b, N, rpc);
-  } else if (mode == SV_UPDATE_GRAM) {
-    if (ds) launch_update<PolDs, true>(b, N, rpc, maxcols, s);
-    else launch_update<PolC64, true>(b, N, rpc, maxcols, s);
+  if (ds) {
+    if (nb == 1) launch_pass_nb<PolDs, 1>(b, mode, N, rpc, maxcols, s);
+    else launch_pass_nb<PolDs, 2>(b, mode, N, rpc, maxcols, s);
   } else {
-    if (ds) launch_update<PolDs, false>(b, N, rpc, maxcols, s);
-    else launch_update<PolC64, false>(b, N, rpc, maxcols, s);
+    if (nb == 1) launch_pass_nb<PolC64, 1>(b, mode, N, rpc, maxcols, s);
+    else launch_pass_nb<PolC64, 2>(b, mode, N, rpc, maxcols, s);
   }
   SWI_CHECK_LAUNCH();
   if (launches) ++*launches;
@@ -330,18 +521,31 @@ void launch_sv_pass(const SvBatch& b, int mode, bool ds, int N, int rpc, cudaStr
 
 void launch_sv_reduce(const SvReduceBatch& b, cudaStream_t s, long long* launches) {
   if (b.n <= 0) return;
-  int maxcols = 1;
-  for (int q = 0; q < b.n; ++q) maxcols = std::max(maxcols, b.job[q].mode == 1 ? 1 : b.job[q].ncols);
-  sv_reduce_kernel<<<dim3((maxcols + 31) / 32, b.n), 256, 0, s>>>(b);
+  int maxent = 1;
+  for (int q = 0; q < b.n; ++q) {
+    const SvReduceJob& J = b.job[q];
+    if (J.nb != 1 && J.nb != 2) throw Error{SWI_EINVAL, "chunk reduction: blocks of 1 or 2 vectors"};
+    if (J.mode != 0 && J.r == nullptr) throw Error{SWI_EINVAL, "chunk reduction: Cholesky output missing"};
+    if (J.mode == 2 && J.nb != 2) throw Error{SWI_EINVAL, "chunk reduction: second Cholesky pass needs nb = 2"};
+    maxent = std::max(maxent, J.mode == 0 ? J.ncols * J.nb : J.nb * J.nb);
+  }
+  sv_reduce_kernel<<<dim3((maxent + 31) / 32, b.n), 32 * kRedLanes, 0, s>>>(b);
   SWI_CHECK_LAUNCH();
   if (launches) ++*launches;
 }
 
-void launch_sv_normalize(const SvNormBatch& b, bool ds, int N, cudaStream_t s, long long* launches) {
+void launch_sv_normalize(const SvNormBatch& b, bool ds, int nb, int N, cudaStream_t s, long long* launches) {
   if (b.n <= 0) return;
+  if (nb != 1 && nb != 2) throw Error{SWI_EINVAL, "normalisation: blocks of 1 or 2 vectors"};
   const int blocks = std::min((N + 255) / 256, 1024);
-  if (ds) sv_normalize_kernel<double2><<<dim3(blocks, b.n), 256, 0, s>>>(b, N);
-  else sv_normalize_kernel<float2><<<dim3(blocks, b.n), 256, 0, s>>>(b, N);
+  const dim3 grid(blocks, b.n);
+  if (ds) {
+    if (nb == 1) sv_normalize_kernel<double2, 1><<<grid, 256, 0, s>>>(b, N);
+    else sv_normalize_kernel<double2, 2><<<grid, 256, 0, s>>>(b, N);
+  } else {
+    if (nb == 1) sv_normalize_kernel<float2, 1><<<grid, 256, 0, s>>>(b, N);
+    else sv_normalize_kernel<float2, 2><<<grid, 256, 0, s>>>(b, N);
+  }
   SWI_CHECK_LAUNCH();
   if (launches) ++*launches;
 }

@@ -1,15 +1,19 @@
-// The windowed solve with single-vector windows (block width 1).
+// The windowed solve with single-vector windows (block width 1) or windows
+// of 2-vector blocks.
 //
-// Each window j runs the single-vector Krylov-Schur iteration on the shifted,
-// never-inverted operator A - sigma_j (Eq. 3) with the 'SM' selection: the
-// exact-shift thick restart that ARPACK's implicitly restarted Arnoldi method
-// performs (Section 2.1), one new basis vector per window and step.  All
-// windows step in lockstep: one stencil launch applies A - sigma_j to the
-// newest vector of every window, and each Gram-Schmidt pass (classical, twice)
-// is one launch over all windows that streams every basis once.  A window
-// whose basis is full runs its projected eigenproblem (schur_ds.cu) on a
-// stream of its own while the others keep expanding, then rotates its basis
-// to the kept Schur vectors.
+// Each window j runs the Krylov-Schur iteration on the shifted, never-inverted
+// operator A - sigma_j (Eq. 3) with the 'SM' selection: the exact-shift thick
+// restart that ARPACK's implicitly restarted Arnoldi method performs (Section
+// 2.1), nb = 1 or 2 new basis vectors per window and step.  A single starting
+// vector spans only one vector of each eigenspace, so eigenvalues of
+// multiplicity two (a wire whose cross-section and potential share a symmetry)
+// need nb = 2 to converge both partners.  All windows step in lockstep: one
+// stencil launch applies A - sigma_j to the newest vectors of every window,
+// and each Gram-Schmidt pass (classical, twice) is one launch over all windows
+// that streams every basis once; a 2-vector block is then orthonormalised by
+// Cholesky-QR, twice.  A window whose basis is full runs its projected
+// eigenproblem (schur_ds.cu) on a stream of its own while the others keep
+// expanding, then rotates its basis to the kept Schur vectors.
 //
 // Two arithmetics share this driver:
 //  - complex128 bases, double-single products and stencil (krylov_sv.cu,
@@ -47,26 +51,29 @@ struct SvWin {
   using T = typename SV<DS>::T;
   double sigma = 0.0;  // the shift the stencil applies (rounded to FP32 in the complex64 form)
   int nreq = 0, m = 0, keep = 0, ldq = 0, ldh = 0, col = 0;
-  int p = 0;           // index of the newest basis vector (the one expanded next)
-  DevMem Q, H, Z, S, Bz, theta, resid, Yw, eps_w, res_w, Hw, Zw, C1, C2, Z32, invb, part;  // part: FP64 chunk partials
+  int p = 0;  // the newest block is basis columns [p, p + nb) (the ones expanded next)
+  DevMem Q, H, Z, S, Bz, theta, resid, Yw, eps_w, res_w, Hw, Zw, C1, C2, Z32, rinv, part;  // part: FP64 chunk partials
   bool done = false, failed = false;
   long long matvecs = 0;
   int restarts = 0, nconv = 0;
 };
 
-// H <- [[T_kk, 0], [b^T, 0]]: keep the leading kk x kk Schur block, put the
-// coupling row b = B Z[:, 0:kk] below it, clear the rest of the (n x n) array.
-__global__ void restart_h_kernel(double2* H, int ldh, int n, int kk, const double2* Bz) {
+// H <- [[T_kk, 0], [Bz, 0]]: keep the leading kk x kk Schur block, put the nb
+// coupling rows Bz = B Z[:, 0:kk] ([nb][ldh]) below it, clear the rest of the
+// (n x n) array.
+__global__ void restart_h_kernel(double2* H, int ldh, int n, int kk, int nb, const double2* Bz) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (long long)n * n) return;
   const int i = (int)(e / n), j = (int)(e % n);
   if (i < kk && j < kk) return;
-  H[(long long)i * ldh + j] = (i == kk && j < kk) ? Bz[j] : make_double2(0.0, 0.0);
+  H[(long long)i * ldh + j] =
+      (i >= kk && i < kk + nb && j < kk) ? Bz[(long long)(i - kk) * ldh + j] : make_double2(0.0, 0.0);
 }
 
-void launch_restart_h(double2* H, int ldh, int n, int kk, const double2* Bz, cudaStream_t s, long long* launches) {
+void launch_restart_h(double2* H, int ldh, int n, int kk, int nb, const double2* Bz, cudaStream_t s,
+                      long long* launches) {
   const long long e = (long long)n * n;
-  restart_h_kernel<<<(unsigned)((e + 255) / 256), 256, 0, s>>>(H, ldh, n, kk, Bz);
+  restart_h_kernel<<<(unsigned)((e + 255) / 256), 256, 0, s>>>(H, ldh, n, kk, nb, Bz);
   SWI_CHECK_LAUNCH();
   if (launches) ++*launches;
 }
@@ -103,6 +110,8 @@ swi_status solve_sv(swi_ctx* c, const swi_solve_opts& opt, swi_solve_info* info)
   using Tr = SV<DS>;
   using T = typename Tr::T;
   using Win = SvWin<DS>;
+  const int nb = opt.block > 0 ? opt.block : 1;
+  if (nb != 1 && nb != 2) return fail(c, SWI_EINVAL, "single-vector windows: blocks of 1 or 2 vectors");
   const double rel_tol = opt.rel_tol > 0 ? opt.rel_tol : 1e-10;
   const double eq_rtol = opt.eq_rtol > 0 ? opt.eq_rtol : (DS ? 1e-8 : 1e-5);
   const double drop_tol = opt.drop_tol > 0 ? opt.drop_tol : (DS ? 1e-6 : 1e-2);
@@ -115,6 +124,7 @@ swi_status solve_sv(swi_ctx* c, const swi_solve_opts& opt, swi_solve_info* info)
   if (!DS) swi::stencil_c64_tma_error(true);
   const double t0 = swi::now_seconds();
   const size_t N = c->N;
+  const int max_basis = nb == 1 ? 1000 : 510;
 
   std::vector<std::unique_ptr<Win>> win(nwin);
   size_t total_out = 0;
@@ -125,18 +135,20 @@ swi_status solve_sv(swi_ctx* c, const swi_solve_opts& opt, swi_solve_info* info)
     w.sigma = DS ? c->sigma[j] : (double)(float)c->sigma[j];
     w.nreq = c->nreq[j];
     w.col = j;
-    int keep = opt.keep > 0 ? opt.keep : std::max(w.nreq + (w.nreq + 1) / 2, w.nreq + 1);
-    // the default basis leaves 128 to 144 new vectors per restart cycle (the
-    // stagger by window index keeps equal windows from restarting together)
-    int m = opt.max_basis > 0 ? opt.max_basis : std::max(2 * w.nreq + 1, keep + 128 + 8 * (j % 3));
-    if (keep > m - 1) keep = m - 1;
+    int keep = opt.keep > 0 ? opt.keep : std::max(w.nreq + (w.nreq + 1) / 2, w.nreq + nb);
+    // the default basis leaves 128 to 144 steps per restart cycle (the stagger
+    // by window index keeps equal windows from restarting together)
+    int m = opt.max_basis > 0 ? opt.max_basis : std::max(2 * w.nreq + 1, keep + nb * (128 + 8 * (j % 3)));
+    if (keep > m - nb) keep = m - nb;
     if (keep < w.nreq) return fail(c, SWI_EINVAL, "max_basis too small for the window request");
-    if (m > 1000) return fail(c, SWI_EINVAL, "single-vector windows: basis of at most 1000 vectors");
-    if (m + 1 > c->N) return fail(c, SWI_EINVAL, "basis larger than the problem dimension");
+    if (m > max_basis)
+      return fail(c, SWI_EINVAL, nb == 1 ? "single-vector windows: basis of at most 1000 vectors"
+                                         : "2-vector blocks: basis of at most 510 vectors");
+    if (m + nb > c->N) return fail(c, SWI_EINVAL, "basis larger than the problem dimension");
     w.m = m;
     w.keep = keep;
-    w.ldq = DS ? (m + 2) / 2 * 2 : (m + 4) / 4 * 4;  // >= m + 1 columns, rows on 32-byte boundaries
-    w.ldh = m + 1;
+    w.ldq = DS ? (m + nb + 1) / 2 * 2 : (m + nb + 3) / 4 * 4;  // >= m + nb columns, rows on 32-byte boundaries
+    w.ldh = m + nb;
     max_m = std::max(max_m, m);
     total_out += w.nreq;
   }
@@ -149,7 +161,7 @@ swi_status solve_sv(swi_ctx* c, const swi_solve_opts& opt, swi_solve_info* info)
     w.H.ensure(sizeof(double2) * hh);
     w.Z.ensure(sizeof(double2) * hh);
     w.S.ensure(sizeof(double2) * hh);
-    w.Bz.ensure(sizeof(double2) * w.ldh);
+    w.Bz.ensure(sizeof(double2) * nb * w.ldh);
     w.theta.ensure(sizeof(double2) * w.ldh);
     w.resid.ensure(sizeof(double) * w.ldh);
     w.Hw.ensure(16 * hh);
@@ -157,30 +169,34 @@ swi_status solve_sv(swi_ctx* c, const swi_solve_opts& opt, swi_solve_info* info)
     w.Yw.ensure(sizeof(double2) * w.ldh * w.nreq);
     w.eps_w.ensure(sizeof(double2) * w.nreq);
     w.res_w.ensure(sizeof(double) * w.nreq);
-    w.C1.ensure(sizeof(double2) * w.ldh);
-    w.C2.ensure(sizeof(double2) * w.ldh);
+    w.C1.ensure(sizeof(double2) * w.ldh * nb);
+    w.C2.ensure(sizeof(double2) * w.ldh * nb);
     if (!DS) w.Z32.ensure(sizeof(float2) * hh);
-    w.invb.ensure(sizeof(double) * 2);
-    w.part.ensure(sizeof(double2) * (size_t)nchunks * w.ldh);
+    w.rinv.ensure(sizeof(double2) * 16);  // R^-1, R, breakdown flag
+    w.part.ensure(sizeof(double2) * (size_t)nchunks * w.ldh * nb);
     SWI_CUDA_TRY(cudaMemsetAsync(w.H.p, 0, sizeof(double2) * hh, c->stream));
     SWI_CUDA_TRY(cudaMemsetAsync(w.Q.p, 0, sizeof(T) * N * w.ldq, c->stream));
+    SWI_CUDA_TRY(cudaMemsetAsync(w.rinv.p, 0, sizeof(double2) * 16, c->stream));
   }
   const int n_all = (int)total_out;
   c->Uall.ensure(sizeof(double2) * N * n_all);
   c->ordinfo.ensure(sizeof(int) * 4 * nwin);
-  // newest vector of every window (column j) and its image under A - sigma_j;
-  // a complex128 work block for the restart rotations and the delivered Ritz vectors
+  // newest block of every window (columns [j nb, j nb + nb)) and its image
+  // under A - sigma_j; a complex128 work block for the restart rotations and
+  // the delivered Ritz vectors
   DevMem Vcur, Wblk, sigt, Tmp;
-  const int ldv = nwin + (nwin & 1);  // even: 16-byte rows for the tensor-map-staged stencil
+  const int ncv = nwin * nb;
+  const int ldv = ncv + (ncv & 1);  // even: 16-byte rows for the tensor-map-staged stencil
   Vcur.ensure(sizeof(T) * N * ldv);
   Wblk.ensure(sizeof(T) * N * ldv);
   SWI_CUDA_TRY(cudaMemsetAsync(Vcur.p, 0, sizeof(T) * N * ldv, c->stream));
-  sigt.ensure(sizeof(double) * std::max(nwin, 4));
-  Tmp.ensure(sizeof(double2) * N * (max_m + 1));
+  sigt.ensure(sizeof(double) * std::max(ncv, 4));
+  Tmp.ensure(sizeof(double2) * N * (max_m + nb));
   {
-    std::vector<typename Tr::Sig> sg(nwin);
-    for (int j = 0; j < nwin; ++j) sg[j] = (typename Tr::Sig)win[j]->sigma;
-    SWI_CUDA_TRY(cudaMemcpyAsync(sigt.p, sg.data(), sizeof(typename Tr::Sig) * nwin, cudaMemcpyHostToDevice,
+    std::vector<typename Tr::Sig> sg(ncv);
+    for (int j = 0; j < nwin; ++j)
+      for (int b = 0; b < nb; ++b) sg[j * nb + b] = (typename Tr::Sig)win[j]->sigma;
+    SWI_CUDA_TRY(cudaMemcpyAsync(sigt.p, sg.data(), sizeof(typename Tr::Sig) * ncv, cudaMemcpyHostToDevice,
                                  c->stream));
     sync(c->stream);
   }
@@ -190,42 +206,75 @@ swi_status solve_sv(swi_ctx* c, const swi_solve_opts& opt, swi_solve_info* info)
     if constexpr (DS) {
       swi::StencilBatch sb;
       sb.n = 0;
-      for (int c0 = 0; c0 < nwin; c0 += 32)
+      for (int c0 = 0; c0 < ncv; c0 += 32)
         sb.blk[sb.n++] = swi::StencilBlock{reinterpret_cast<const double2*>(Vcur.p) + c0,
                                            reinterpret_cast<double2*>(Wblk.p) + c0, ldv, ldv,
-                                           std::min(32, nwin - c0), c0};
+                                           std::min(32, ncv - c0), c0};
       swi::launch_stencil_ds(P64, sb, sigt.as<double>(), c->stream, &c->launches);
     } else {
-      swi::launch_stencil_c64(P32, Vcur.as<float2>(), ldv, Wblk.as<float2>(), ldv, nwin, sigt.as<float>(),
+      swi::launch_stencil_c64(P32, Vcur.as<float2>(), ldv, Wblk.as<float2>(), ldv, ncv, sigt.as<float>(),
                               c->stream, &c->launches);
     }
   };
+  // Orthonormalise the blocks W[:, j nb : j nb + nb] of the given windows
+  // after their last Gram-Schmidt pass has left w^H w in the chunk partials
+  // (part): one Cholesky factor for nb = 1, Cholesky-QR twice for nb = 2; R
+  // goes below the block's column of H (when hrow is set), the block into the
+  // basis at column dst_col and into Vcur.
+  auto orthonormalise = [&](const std::vector<Win*>& ws, const std::vector<int>& dst_col, bool hrow) {
+    const int na = (int)ws.size();
+    swi::SvReduceBatch r1, r2;
+    swi::SvNormBatch n1, n2;
+    swi::SvBatch g;
+    r1.n = r2.n = n1.n = n2.n = g.n = na;
+    for (int q = 0; q < na; ++q) {
+      Win& w = *ws[q];
+      T* wc = Wblk.as<T>() + w.col * nb;
+      T* Qd = w.Q.template as<T>() + dst_col[q];
+      double2* Hr = hrow ? w.H.template as<double2>() + (long long)(w.p + nb) * w.ldh + w.p : nullptr;
+      double2* pp = w.part.template as<double2>();
+      double2* ri = w.rinv.template as<double2>();
+      r1.job[q] = swi::SvReduceJob{pp, w.ldh * nb, nchunks, 0, nb, 1, nullptr, nb == 1 ? Hr : nullptr, w.ldh, ri};
+      g.job[q] = swi::SvJob{w.Q.p, w.ldq, 0, wc, ldv, nullptr, pp, w.ldh * nb};
+      r2.job[q] = swi::SvReduceJob{pp, w.ldh * nb, nchunks, 0, nb, 2, nullptr, Hr, w.ldh, ri};
+      if (nb == 1) {
+        n1.job[q] = swi::SvNormJob{wc, ldv, Qd, w.ldq, Vcur.as<T>() + w.col * nb, ldv, ri};
+      } else {
+        n1.job[q] = swi::SvNormJob{wc, ldv, wc, ldv, nullptr, 0, ri};
+        n2.job[q] = swi::SvNormJob{wc, ldv, Qd, w.ldq, Vcur.as<T>() + w.col * nb, ldv, ri};
+      }
+    }
+    swi::launch_sv_reduce(r1, c->stream, &c->launches);
+    swi::launch_sv_normalize(n1, DS, nb, c->N, c->stream, &c->launches);
+    if (nb == 1) return;
+    swi::launch_sv_pass(g, swi::SV_UPDATE_NORM, DS, nb, c->N, rpc, c->stream, &c->launches);
+    swi::launch_sv_reduce(r2, c->stream, &c->launches);
+    swi::launch_sv_normalize(n2, DS, nb, c->N, c->stream, &c->launches);
+  };
 
-  // start vectors: random, normalised, in column 0 of each basis and in Vcur
+  // start blocks: random, orthonormalised, in columns [0, nb) of each basis and in Vcur
   {
     swi::SvBatch gb;
-    swi::SvReduceBatch rb;
-    swi::SvNormBatch nb;
-    gb.n = rb.n = nb.n = nwin;
+    gb.n = nwin;
+    std::vector<Win*> all;
+    std::vector<int> zero(nwin, 0);
     for (int j = 0; j < nwin; ++j) {
       Win& w = *win[j];
-      if constexpr (DS)
-        random_col_c128_kernel<<<std::min((c->N + 255) / 256, 1024), 256, 0, c->stream>>>(
-            Wblk.as<double2>() + j, ldv, c->N, seed * 1000003ull + j);
-      else
-        swi::launch_random_col_c64(Wblk.as<float2>() + j, ldv, c->N, seed * 1000003ull + j, c->stream, &c->launches);
-      SWI_CHECK_LAUNCH();
-      SWI_CUDA_TRY(cudaMemsetAsync(w.C2.p, 0, sizeof(double2), c->stream));
-      gb.job[j] = swi::SvJob{w.Q.p, w.ldq, 1, Wblk.as<T>() + j, ldv, w.C2.template as<double2>(),
-                             w.part.template as<double2>(), w.ldh};
-      rb.job[j] = swi::SvReduceJob{w.part.template as<double2>(), w.ldh, nchunks, 1, 1, nullptr, nullptr, 0,
-                                   w.invb.template as<double>()};
-      nb.job[j] = swi::SvNormJob{Wblk.as<T>() + j, ldv, w.Q.p, w.ldq, Vcur.as<T>() + j, ldv, w.invb.template as<double>()};
+      all.push_back(&w);
+      for (int b = 0; b < nb; ++b) {
+        const unsigned long long sd = seed * 1000003ull + (unsigned long long)j * nb + b;
+        if constexpr (DS)
+          random_col_c128_kernel<<<std::min((c->N + 255) / 256, 1024), 256, 0, c->stream>>>(
+              Wblk.as<double2>() + j * nb + b, ldv, c->N, sd);
+        else
+          swi::launch_random_col_c64(Wblk.as<float2>() + j * nb + b, ldv, c->N, sd, c->stream, &c->launches);
+        SWI_CHECK_LAUNCH();
+      }
+      gb.job[j] = swi::SvJob{w.Q.p, w.ldq, 0, Wblk.as<T>() + j * nb, ldv, nullptr, w.part.template as<double2>(),
+                             w.ldh * nb};
     }
-    // ||w||^2 (the update by a zero basis column is a no-op)
-    swi::launch_sv_pass(gb, swi::SV_UPDATE_NORM, DS, c->N, rpc, c->stream, &c->launches);
-    swi::launch_sv_reduce(rb, c->stream, &c->launches);
-    swi::launch_sv_normalize(nb, DS, c->N, c->stream, &c->launches);
+    swi::launch_sv_pass(gb, swi::SV_UPDATE_NORM, DS, nb, c->N, rpc, c->stream, &c->launches);
+    orthonormalise(all, zero, false);
   }
 
   const double tol_abs = rel_tol * anorm;
@@ -267,13 +316,14 @@ swi_status solve_sv(swi_ctx* c, const swi_solve_opts& opt, swi_solve_info* info)
   for (auto& e : side.lag) SWI_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   std::vector<int> in_schur(nwin, 0);
 
-  // the window's basis as complex128 [N][ld] (the complex64 form widens it into Tmp)
-  auto basis64 = [&](Win& w, int& ld) -> const double2* {
+  // the window's first ncol basis columns as complex128 [N][ld] (the complex64
+  // form widens them into Tmp)
+  auto basis64 = [&](Win& w, int ncol, int& ld) -> const double2* {
     if constexpr (DS) {
       ld = w.ldq;
       return w.Q.template as<double2>();
     } else {
-      swi::launch_widen(w.Q.template as<float2>(), w.ldq, Tmp.as<double2>(), w.ldh, c->N, w.m, c->stream,
+      swi::launch_widen(w.Q.template as<float2>(), w.ldq, Tmp.as<double2>(), w.ldh, c->N, ncol, c->stream,
                         &c->launches);
       ld = w.ldh;
       return Tmp.as<double2>();
@@ -284,57 +334,60 @@ swi_status solve_sv(swi_ctx* c, const swi_solve_opts& opt, swi_solve_info* info)
     Win& w = *win[j];
     const int* oi = side.oi + 4 * j;
     const int kk = oi[0], nconv = oi[1], st = oi[2];
+    const int n = w.p;  // order of the projected matrix
     SWI_CUDA_TRY(cudaStreamWaitEvent(c->stream, side.done[j], 0));
     w.restarts++;
     w.nconv = nconv;
-    if (c->prof_on) c->schur_flops += 64.0 / 3.0 * (double)w.m * w.m * w.m + 20.0 * 1024.0 * (double)oi[3];
+    if (c->prof_on) c->schur_flops += 64.0 / 3.0 * (double)n * n * n + 20.0 * 1024.0 * (double)oi[3];
     if (st != 0) w.failed = true;
     if (st != 0 || nconv >= w.nreq || w.matvecs >= budget) {
       // Ritz vectors of the wanted pairs into Uall (complex128)
       int ldb = 0;
-      const double2* Qb = basis64(w, ldb);
+      const double2* Qb = basis64(w, n, ldb);
       swi::RitzBatch fin;
       fin.n = 1;
       fin.job[0] = swi::RitzJob{w.Z.template as<double2>(), w.S.template as<double2>(), w.theta.template as<double2>(),
                                 w.resid.template as<double>(), c->ordinfo.as<int>() + 4 * j, w.Yw.template as<double2>(),
-                                w.eps_w.template as<double2>(), w.res_w.template as<double>(), w.m, w.ldh, w.nreq,
+                                w.eps_w.template as<double2>(), w.res_w.template as<double>(), n, w.ldh, w.nreq,
                                 w.nreq, w.sigma};
       swi::RowGemmBatch rb;
       rb.n = 1;
       rb.job[0] = swi::RowGemmJob{Qb, w.Yw.template as<double2>(), nullptr, c->Uall.as<double2>() + out_off[j], ldb,
-                                  w.nreq, 0, n_all, w.m, w.nreq, 1.0, 0.0};
-      ProfScope ps(c, SWI_K_ROTATE, 8.0 * c->N * (double)w.m * w.nreq, 16.0 * c->N * (double)(w.m + w.nreq));
+                                  w.nreq, 0, n_all, n, w.nreq, 1.0, 0.0};
+      ProfScope ps(c, SWI_K_ROTATE, 8.0 * c->N * (double)n * w.nreq, 16.0 * c->N * (double)(n + w.nreq));
       swi::launch_ritz_batch(fin, c->stream, &c->launches);
       rowgemm_dispatch(SWI_ARITH_DS, rb, c->N, c->stream, &c->launches);
       w.done = true;
       return;
     }
-    if (kk + 1 > w.m || kk < w.nreq) throw Error{SWI_ECUDA, "internal: restart size out of range"};
+    if (kk + nb > w.m || kk < w.nreq || kk > n) throw Error{SWI_ECUDA, "internal: restart size out of range"};
     {
-      // thick restart: Q[:, 0:kk] = Q[:, 0:m] Z[:, 0:kk], the residual vector q_m becomes column kk
-      ProfScope ps(c, SWI_K_ROTATE, 8.0 * c->N * (double)w.m * kk, sizeof(T) * c->N * (double)(w.m + kk));
+      // thick restart: Q[:, 0:kk] = Q[:, 0:n] Z[:, 0:kk]; the residual block
+      // (columns [n, n + nb), also held in Vcur) becomes columns [kk, kk + nb)
+      ProfScope ps(c, SWI_K_ROTATE, 8.0 * c->N * (double)n * kk, sizeof(T) * c->N * (double)(n + kk));
       if constexpr (DS) {
         swi::RowGemmBatch rb;
         rb.n = 1;
         rb.job[0] = swi::RowGemmJob{w.Q.template as<double2>(), w.Z.template as<double2>(), nullptr,
-                                    Tmp.as<double2>(), w.ldq, w.ldh, 0, w.ldh, w.m, kk, 1.0, 0.0};
+                                    Tmp.as<double2>(), w.ldq, w.ldh, 0, w.ldh, n, kk, 1.0, 0.0};
         rowgemm_dispatch(SWI_ARITH_DS, rb, c->N, c->stream, &c->launches);
         swi::launch_copy_block(Tmp.as<double2>(), w.ldh, w.Q.template as<double2>(), w.ldq, c->N, kk, c->stream,
                                &c->launches);
-        swi::launch_copy_block(w.Q.template as<double2>() + w.m, w.ldq, w.Q.template as<double2>() + kk, w.ldq, c->N,
-                               1, c->stream, &c->launches);
+        swi::launch_copy_block(Vcur.as<double2>() + w.col * nb, ldv, w.Q.template as<double2>() + kk, w.ldq, c->N,
+                               nb, c->stream, &c->launches);
       } else {
-        swi::launch_z_to_c64(w.Z.template as<double2>(), w.ldh, w.m, kk, w.Z32.template as<float2>(), kk, c->stream,
+        swi::launch_z_to_c64(w.Z.template as<double2>(), w.ldh, n, kk, w.Z32.template as<float2>(), kk, c->stream,
                              &c->launches);
-        swi::launch_c64_rotate_inplace(w.Q.template as<float2>(), w.ldq, c->N, w.m, w.Z32.template as<float2>(), kk,
+        swi::launch_c64_rotate_inplace(w.Q.template as<float2>(), w.ldq, c->N, n, w.Z32.template as<float2>(), kk,
                                        kk, c->stream, &c->launches);
-        swi::launch_copy_col_c64(w.Q.template as<float2>() + w.m, w.ldq, w.Q.template as<float2>() + kk, w.ldq, c->N,
-                                 c->stream, &c->launches);
+        for (int b = 0; b < nb; ++b)
+          swi::launch_copy_col_c64(Vcur.as<float2>() + w.col * nb + b, ldv, w.Q.template as<float2>() + kk + b,
+                                   w.ldq, c->N, c->stream, &c->launches);
       }
-      launch_restart_h(w.H.template as<double2>(), w.ldh, w.ldh, kk, w.Bz.template as<double2>(), c->stream,
+      launch_restart_h(w.H.template as<double2>(), w.ldh, w.ldh, kk, nb, w.Bz.template as<double2>(), c->stream,
                        &c->launches);
     }
-    w.p = kk;  // the newest vector (already in Vcur) is q_m, now column kk
+    w.p = kk;  // the newest block (already in Vcur) is now columns [kk, kk + nb)
   };
 
   const long long max_steps = 100000000LL;
@@ -366,69 +419,68 @@ swi_status solve_sv(swi_ctx* c, const swi_solve_opts& opt, swi_solve_info* info)
     }
     const int na = (int)act.size();
     const double Nn = (double)c->N;
-    // 1) W[:, j] = (A - sigma_j) q_p for every window (columns of waiting windows are ignored)
+    // 1) W[:, j nb : j nb + nb] = (A - sigma_j) Q_j[:, p : p + nb] for every window
+    //    (columns of waiting windows are computed and ignored)
     {
-      ProfScope ps(c, SWI_K_STENCIL, kStencilFlops * Nn * nwin, (2.0 * sizeof(T) * nwin + 8.0) * Nn);
+      ProfScope ps(c, SWI_K_STENCIL, kStencilFlops * Nn * ncv, (2.0 * sizeof(T) * ncv + 8.0) * Nn);
       apply_all();
     }
-    // 2) classical Gram-Schmidt twice against Q[:, 0:p+1], then the norm:
-    //    Gram, update fused with the second Gram, update fused with the norm
+    // 2) classical Gram-Schmidt twice against Q[:, 0:p+nb], then w^H w:
+    //    Gram, update fused with the second Gram, update fused with w^H w
     double ncol = 0.0;
     swi::SvBatch g0, g1, g2;
-    swi::SvReduceBatch r0, r1, r2;
-    swi::SvNormBatch nb;
-    g0.n = g1.n = g2.n = r0.n = r1.n = r2.n = nb.n = na;
+    swi::SvReduceBatch r0, r1;
+    g0.n = g1.n = g2.n = r0.n = r1.n = na;
+    std::vector<int> dst(na);
     for (int q = 0; q < na; ++q) {
       Win& w = *act[q];
-      if (w.p + 1 > w.m) throw Error{SWI_ECUDA, "internal: Krylov vector beyond the basis buffer"};
-      const int nc = w.p + 1;
+      if (w.p + 2 * nb > w.ldq || w.p + 2 * nb > w.ldh)
+        throw Error{SWI_ECUDA, "internal: Krylov block beyond the basis buffer"};
+      const int nc = w.p + nb;
       ncol += nc;
-      T* Qp = w.Q.template as<T>();
-      T* wc = Wblk.as<T>() + w.col;
+      const void* Qp = w.Q.p;
+      T* wc = Wblk.as<T>() + w.col * nb;
       double2* pp = w.part.template as<double2>();
-      double2* H = w.H.template as<double2>();
-      double2* hcol = H + w.p;
-      g0.job[q] = swi::SvJob{Qp, w.ldq, nc, wc, ldv, nullptr, pp, w.ldh};
-      g1.job[q] = swi::SvJob{Qp, w.ldq, nc, wc, ldv, w.C1.template as<double2>(), pp, w.ldh};
-      g2.job[q] = swi::SvJob{Qp, w.ldq, nc, wc, ldv, w.C2.template as<double2>(), pp, w.ldh};
-      r0.job[q] = swi::SvReduceJob{pp, w.ldh, nchunks, nc, 0, w.C1.template as<double2>(), hcol, w.ldh, nullptr};
-      r1.job[q] = swi::SvReduceJob{pp, w.ldh, nchunks, nc, 0, w.C2.template as<double2>(), hcol, w.ldh, nullptr};
-      r2.job[q] = swi::SvReduceJob{pp, w.ldh, nchunks, 1, 1, nullptr, H + (long long)(w.p + 1) * w.ldh + w.p, 0,
-                                   w.invb.template as<double>()};
-      nb.job[q] = swi::SvNormJob{wc, ldv, Qp + w.p + 1, w.ldq, Vcur.as<T>() + w.col, ldv, w.invb.template as<double>()};
+      double2* hcol = w.H.template as<double2>() + w.p;
+      const int ldp = w.ldh * nb;
+      g0.job[q] = swi::SvJob{Qp, w.ldq, nc, wc, ldv, nullptr, pp, ldp};
+      g1.job[q] = swi::SvJob{Qp, w.ldq, nc, wc, ldv, w.C1.template as<double2>(), pp, ldp};
+      g2.job[q] = swi::SvJob{Qp, w.ldq, nc, wc, ldv, w.C2.template as<double2>(), pp, ldp};
+      r0.job[q] = swi::SvReduceJob{pp, ldp, nchunks, nc, nb, 0, w.C1.template as<double2>(), hcol, w.ldh, nullptr};
+      r1.job[q] = swi::SvReduceJob{pp, ldp, nchunks, nc, nb, 0, w.C2.template as<double2>(), hcol, w.ldh, nullptr};
+      dst[q] = w.p + nb;
     }
     {
-      ProfScope ps(c, SWI_K_GRAM, 2.0 * 8.0 * Nn * ncol, 2.0 * sizeof(T) * Nn * ncol);
-      swi::launch_sv_pass(g0, swi::SV_GRAM, DS, c->N, rpc, c->stream, &c->launches);
+      ProfScope ps(c, SWI_K_GRAM, 2.0 * 8.0 * Nn * ncol * nb, 2.0 * sizeof(T) * Nn * ncol);
+      swi::launch_sv_pass(g0, swi::SV_GRAM, DS, nb, c->N, rpc, c->stream, &c->launches);
       swi::launch_sv_reduce(r0, c->stream, &c->launches);
-      swi::launch_sv_pass(g1, swi::SV_UPDATE_GRAM, DS, c->N, rpc, c->stream, &c->launches);
+      swi::launch_sv_pass(g1, swi::SV_UPDATE_GRAM, DS, nb, c->N, rpc, c->stream, &c->launches);
       swi::launch_sv_reduce(r1, c->stream, &c->launches);
     }
     {
-      ProfScope ps(c, SWI_K_UPDATE, 8.0 * Nn * ncol, sizeof(T) * Nn * ncol + 2.0 * sizeof(T) * Nn * na);
-      swi::launch_sv_pass(g2, swi::SV_UPDATE_NORM, DS, c->N, rpc, c->stream, &c->launches);
-      swi::launch_sv_reduce(r2, c->stream, &c->launches);
-      swi::launch_sv_normalize(nb, DS, c->N, c->stream, &c->launches);
+      ProfScope ps(c, SWI_K_UPDATE, 8.0 * Nn * ncol * nb, sizeof(T) * Nn * ncol + 2.0 * sizeof(T) * Nn * na * nb);
+      swi::launch_sv_pass(g2, swi::SV_UPDATE_NORM, DS, nb, c->N, rpc, c->stream, &c->launches);
+      orthonormalise(act, dst, true);
     }
-    // 3) windows whose basis is full: projected eigenproblem on their own stream
+    // 3) windows whose next block would not fit: projected eigenproblem on their own stream
     for (int q = 0; q < na; ++q) {
       Win& w = *act[q];
       const int j = w.col;
-      w.p += 1;
-      w.matvecs += 1;
-      if (w.p < w.m) continue;
+      w.p += nb;
+      w.matvecs += nb;
+      if (w.p + nb <= w.m) continue;
       // as ARPACK does, keep more Ritz vectors once some wanted pairs have converged
-      const int keep_eff = std::min(w.m - 1, w.keep + std::min(w.nconv, (w.m - w.keep) / 2));
+      const int keep_eff = std::min(w.m - nb, w.keep + std::min(w.nconv, (w.m - w.keep) / 2));
       cudaStream_t sj = side.st[j];
       SWI_CUDA_TRY(cudaEventRecord(side.ready[j], c->stream));
       SWI_CUDA_TRY(cudaStreamWaitEvent(sj, side.ready[j], 0));
       swi::SchurBatch sb;
       sb.n = 1;
-      // B: the coupling row of the Arnoldi relation, row m of H (only H[m][m-1] = beta is nonzero)
+      // B: the nb coupling rows of the Arnoldi relation, rows [p, p + nb) of H
       double2* H = w.H.template as<double2>();
-      sb.job[0] = swi::SchurJob{H, w.Z.template as<double2>(), H + (long long)w.m * w.ldh, w.Bz.template as<double2>(),
+      sb.job[0] = swi::SchurJob{H, w.Z.template as<double2>(), H + (long long)w.p * w.ldh, w.Bz.template as<double2>(),
                                 w.theta.template as<double2>(), w.resid.template as<double>(), w.S.template as<double2>(),
-                                c->ordinfo.as<int>() + 4 * j, w.m, w.ldh, 1, keep_eff, w.nreq, w.m - 1, tol_abs,
+                                c->ordinfo.as<int>() + 4 * j, w.p, w.ldh, nb, keep_eff, w.nreq, w.m - nb, tol_abs,
                                 w.Hw.p, w.Zw.p};
       {
         ProfScope ps(c, SWI_K_SCHUR, 0.0, 0.0, sj);
@@ -446,7 +498,7 @@ swi_status solve_sv(swi_ctx* c, const swi_solve_opts& opt, swi_solve_info* info)
   std::vector<double2> eps_all(n_all);
   std::vector<int> win_of(n_all);
   c->winfo.assign(nwin, swi_window_info());
-  bool any_fail = false, any_noconv = false;
+  bool any_fail = false, any_noconv = false, any_breakdown = false;
   for (int j = 0; j < nwin; ++j) {
     Win& w = *win[j];
     std::vector<double> rw(w.nreq);
@@ -465,6 +517,9 @@ swi_status solve_sv(swi_ctx* c, const swi_solve_opts& opt, swi_solve_info* info)
     double mr = 0.0;
     for (double r : rw) mr = std::max(mr, r / anorm);
     wi.max_res = mr;
+    double2 flag;
+    SWI_CUDA_TRY(cudaMemcpy(&flag, w.rinv.template as<double2>() + 8, sizeof(double2), cudaMemcpyDeviceToHost));
+    if (flag.x != 0.0) any_breakdown = true;
     any_fail |= w.failed;
     any_noconv |= (w.nconv < w.nreq);
   }
@@ -475,6 +530,7 @@ swi_status solve_sv(swi_ctx* c, const swi_solve_opts& opt, swi_solve_info* info)
   const double t1 = swi::now_seconds();
   int minfo[4];
   merge_pairs(c, c->Uall.as<double2>(), n_all, eps_all, win_of, nwin, eq_rtol, drop_tol, opt.n_keep, minfo);
+  record_windows(c, eps_all, win_of, nwin);
   const int nout = minfo[0];
   c->Uall.release();
   {
@@ -505,6 +561,7 @@ swi_status solve_sv(swi_ctx* c, const swi_solve_opts& opt, swi_solve_info* info)
   if (!DS && swi::stencil_c64_tma_error(true))
     return fail(c, SWI_ETIMEOUT, "a stencil block gave up waiting for its tensor-map copy");
   if (any_fail) return fail(c, SWI_ENOCONV, "a window's projected eigenproblem did not converge");
+  if (any_breakdown) return fail(c, SWI_ENOCONV, "a window's new Krylov vectors became linearly dependent");
   if (minfo[3] != 0) return fail(c, SWI_EINVAL, "merge: equal-eigenvalue component too large");
   if (any_noconv) return fail(c, SWI_ENOCONV, "some window did not converge within its matvec budget");
   if (nconv < nout) return fail(c, SWI_ENOCONV, "pairs above rel_tol in the explicit FP64 residual check");

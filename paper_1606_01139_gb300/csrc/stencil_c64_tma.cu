@@ -10,10 +10,10 @@
 //  - plane z of the tile with its 6-point halo (a 44 x 20 x 4 box) arrives in
 //    shared memory by one cp.async.bulk.tensor load, three planes in flight in
 //    a ring of stages, each completed on an mbarrier;
-//  - each thread computes a 2 x 2 patch of points for one column: the x- and
-//    y-neighbours of the patch come from two 14-value strips per direction
-//    (14 shared loads per output instead of 24), the 12 z-neighbours from a
-//    register queue filled by loads one plane ahead;
+//  - each thread computes two points stacked in y for one column: the
+//    y-neighbours of the pair come from one 14-value strip (19 shared loads
+//    per output instead of 24), the 12 z-neighbours from a register queue
+//    filled by loads two planes ahead (512 threads, 16 warps per SM);
 //  - the arithmetic is packed FP32x2 (re, im together).
 // Ghost points: the tensor map fills out-of-range coordinates with zeros (the
 // zero rule, and the planes -1 and n of the odd rule); odd-reflection ghosts
@@ -34,7 +34,7 @@ namespace {
 constexpr int kTX = 32, kTY = 8, kR = 6, kNC = 4;
 constexpr int kBX = kTX + 2 * kR, kBY = kTY + 2 * kR;  // staged box (44 x 20 points)
 constexpr int kStages = 3;
-constexpr int kThreads = (kTX / 2) * (kTY / 2) * kNC;  // 256: a 2 x 2 patch per thread
+constexpr int kThreads = kTX * (kTY / 2) * kNC;  // 512: two points (y, y + 1) per thread
 constexpr int kStageFloats = kBY * kBX * kNC * 2;       // 7040 floats = 28,160 bytes
 constexpr unsigned kStageBytes = kStageFloats * 4;
 constexpr long long kSpinLimit = 1LL << 26;  // ~ seconds of polling: a lost copy, not a slow one
@@ -123,24 +123,24 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ int s_nghost;
   const int tid = threadIdx.x;
   const int cc = tid % kNC;
-  const int px = (tid / kNC) % (kTX / 2);
-  const int py = tid / (kNC * (kTX / 2));
+  const int px = (tid / kNC) % kTX;
+  const int py = tid / (kNC * kTX);
   const int g = blockIdx.x % cgroups;
   const int tile = blockIdx.x / cgroups;
   const int x0 = (tile % tiles_x) * kTX, y0 = (tile / tiles_x) * kTY;
   const int c0 = g * kNC, c = c0 + cc;
   const int z0 = blockIdx.y * zchunk, z1 = min(P.nz, z0 + zchunk);
-  const int xa = x0 + 2 * px, ya = y0 + 2 * py;  // the patch's first point
+  const int xa = x0 + px, ya = y0 + 2 * py;  // the pair's first point
   const long long plane = (long long)P.nx * P.ny;
   const long long plane_ld = plane * ldx;
   const bool colok = c < ncols;
-  bool ok[2][2];
-  long long ptc[2][2];
+  bool ok[2][1];
+  long long ptc[2][1];
 #pragma unroll
   for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
-    for (int dx = 0; dx < 2; ++dx) {
-      ok[dy][dx] = colok && xa + dx < P.nx && ya + dy < P.ny;
+    for (int dx = 0; dx < 1; ++dx) {
+      ok[dy][dx] = colok && xa + dx < P.nx && ya + dy < P.ny;  // dx = 0: one point per row
       ptc[dy][dx] = ((long long)(ya + dy) * P.nx + (xa + dx)) * ldx + c;
     }
   float cm[kR + 1];
@@ -188,21 +188,24 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int z = z0; z < min(z1, z0 + kStages - 1); ++z) issue(z);
   }
 
-  // z queues of the four points, a ring of 13 planes: plane z0 - 6 + k in slot k
+  // z queues of the two points, a ring of 13 planes: plane z0 - 6 + k in slot k
   // (mod 13); the z loop is unrolled by 13 so every slot index is a constant
-  float2 q[2][2][2 * kR + 1];
+  float2 q[2][1][2 * kR + 1];
 #pragma unroll
   for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
-    for (int dx = 0; dx < 2; ++dx)
+    for (int dx = 0; dx < 1; ++dx)
 #pragma unroll
       for (int k = 0; k < 2 * kR + 1; ++k) q[dy][dx][k] = load_z<BC>(X, ptc[dy][dx], plane_ld, z0 - kR + k, P.nz, ok[dy][dx]);
 
-  float vnext[2][2], gnext[2][2];
+  float vnext[2][1], gnext[2][1];
+  float2 nq1[2][1];
+#pragma unroll
+  for (int dy = 0; dy < 2; ++dy) nq1[dy][0] = load_z<BC>(X, ptc[dy][0], plane_ld, z0 + kR + 1, P.nz, ok[dy][0]);
 #pragma unroll
   for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
-    for (int dx = 0; dx < 2; ++dx) {
+    for (int dx = 0; dx < 1; ++dx) {
       const long long pi = (long long)z0 * plane + (long long)(ya + dy) * P.nx + (xa + dx);
       vnext[dy][dx] = ok[dy][dx] ? __ldg(P.V + pi) : 0.f;
       gnext[dy][dx] = ok[dy][dx] ? __ldg(P.G + pi) : 0.f;
@@ -217,15 +220,16 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (zs >= z1) break;
       const int s = (zs - z0) % kStages;
       const unsigned parity = (unsigned)(((zs - z0) / kStages) & 1);
-      // the next plane's queue entries and the local potential of the next plane,
-      // loaded before the wait (this plane's potential came one step earlier)
-      float2 nq[2][2];
-      float vv[2][2], gg[2][2];
+      // queue entries two planes ahead and the local potential one plane ahead,
+      // loaded before the wait
+      float vv[2][1], gg[2][1];
+      float2 nq[2][1];
 #pragma unroll
       for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
-        for (int dx = 0; dx < 2; ++dx) {
-          nq[dy][dx] = load_z<BC>(X, ptc[dy][dx], plane_ld, zs + kR + 1, P.nz, ok[dy][dx]);
+        for (int dx = 0; dx < 1; ++dx) {
+          nq[dy][dx] = nq1[dy][dx];
+          nq1[dy][dx] = load_z<BC>(X, ptc[dy][dx], plane_ld, zs + kR + 2, P.nz, ok[dy][dx]);
           vv[dy][dx] = vnext[dy][dx];
           gg[dy][dx] = gnext[dy][dx];
           const long long pi = (long long)(zs + 1) * plane + (long long)(ya + dy) * P.nx + (xa + dx);
@@ -250,33 +254,27 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncthreads();
       }
       constexpr int Q = 2 * kR + 1;
-      float2 acc[2][2];
+      float2 acc[2][1];
 #pragma unroll
       for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
-        for (int dx = 0; dx < 2; ++dx) {
+        for (int dx = 0; dx < 1; ++dx) {
           const float2 u = q[dy][dx][(kR + j) % Q];
           const float d = dcen + vv[dy][dx], gm = gg[dy][dx];
           acc[dy][dx] = make_float2(fmaf(d, u.x, gm * u.y), fmaf(d, u.y, -gm * u.x));
         }
-      // x strips (rows of the patch): 14 values serve both points of the row
+      // x neighbours of each point (13 values of its row)
 #pragma unroll
       for (int dy = 0; dy < 2; ++dy) {
-        float2 sx[2 * kR + 2];
-        const float2* row = S2 + ((2 * py + dy + kR) * kBX + 2 * px) * kNC + cc;
+        const float2* row = S2 + ((2 * py + dy + kR) * kBX + px) * kNC + cc;
 #pragma unroll
-        for (int k = 0; k < 2 * kR + 2; ++k) sx[k] = row[k * kNC];
-#pragma unroll
-        for (int dx = 0; dx < 2; ++dx)
-#pragma unroll
-          for (int m = 1; m <= kR; ++m)
-            acc[dy][dx] = __ffma2_rn(make_float2(cm[m], cm[m]), f2add(sx[dx + kR - m], sx[dx + kR + m]), acc[dy][dx]);
+        for (int m = 1; m <= kR; ++m)
+          acc[dy][0] = __ffma2_rn(make_float2(cm[m], cm[m]), f2add(row[(kR - m) * kNC], row[(kR + m) * kNC]), acc[dy][0]);
       }
-      // y strips (columns of the patch) together with the z queue
-#pragma unroll
-      for (int dx = 0; dx < 2; ++dx) {
+      // y strip of the pair (14 values), together with the z queues
+      {
         float2 sy[2 * kR + 2];
-        const float2* colp = S2 + ((2 * py) * kBX + 2 * px + dx + kR) * kNC + cc;
+        const float2* colp = S2 + ((2 * py) * kBX + px + kR) * kNC + cc;
 #pragma unroll
         for (int k = 0; k < 2 * kR + 2; ++k) sy[k] = colp[k * kBX * kNC];
 #pragma unroll
@@ -284,14 +282,14 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int m = 1; m <= kR; ++m) {
             const float2 t = f2add(f2add(sy[dy + kR - m], sy[dy + kR + m]),
-                                   f2add(q[dy][dx][(kR - m + j) % Q], q[dy][dx][(kR + m + j) % Q]));
-            acc[dy][dx] = __ffma2_rn(make_float2(cm[m], cm[m]), t, acc[dy][dx]);
+                                   f2add(q[dy][0][(kR - m + j) % Q], q[dy][0][(kR + m + j) % Q]));
+            acc[dy][0] = __ffma2_rn(make_float2(cm[m], cm[m]), t, acc[dy][0]);
           }
       }
 #pragma unroll
       for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
-        for (int dx = 0; dx < 2; ++dx) {
+        for (int dx = 0; dx < 1; ++dx) {
           if (ok[dy][dx]) Y[((long long)zs * plane + (long long)(ya + dy) * P.nx + (xa + dx)) * ldy + c] = acc[dy][dx];
           q[dy][dx][j % Q] = nq[dy][dx];  // plane zs + 7 replaces plane zs - 6
         }

@@ -270,9 +270,11 @@ void launch_sub_diag(double2* Y, int ldy, const double2* X, int ldx, const doubl
                      cudaStream_t s, long long* launches);
 
 // ---------------------------------------------------------------- single-vector Krylov loop
-// (krylov_sv.cu).  Per job (window): Q [N][ldq] basis columns [0, ncols)
-// (complex64 or complex128), w a column of a [N][ldw] block of the same type,
-// c ncols FP64 coefficients, part [nchunks][ldp] FP64 chunk partials.
+// (krylov_sv.cu), also with blocks of nb = 2 new vectors per window and step.
+// Per job (window): Q [N][ldq] basis columns [0, ncols) (complex64 or
+// complex128; ncols may be 0), w the nb adjacent columns of a [N][ldw] block of
+// the same type, c the [ncols][nb] FP64 coefficients, part [nchunks][ldp] FP64
+// chunk partials.
 enum { SV_GRAM = 0, SV_UPDATE_GRAM = 1, SV_UPDATE_NORM = 2 };
 struct SvJob {
   const void* Q;
@@ -287,26 +289,34 @@ struct SvBatch {
   int n;
   SvJob job[kMaxBatch];
 };
-// SV_GRAM: part = Q^H w; SV_UPDATE_GRAM: w -= Q c, then part = Q^H w;
-// SV_UPDATE_NORM: w -= Q c, then part[.][0] = ||w||^2.  ds: complex128 in
-// double-single arithmetic, else complex64 in FP32.
-void launch_sv_pass(const SvBatch& b, int mode, bool ds, int N, int rpc, cudaStream_t s, long long* launches);
-// rows per chunk for njobs windows (64 to 1024, a multiple of 8)
+// SV_GRAM: part = Q^H w ([ncols][nb]); SV_UPDATE_GRAM: w -= Q c, then
+// part = Q^H w; SV_UPDATE_NORM: w -= Q c, then part = w^H w ([nb][nb]).
+// ds: complex128 in double-single arithmetic, else complex64 in FP32.
+void launch_sv_pass(const SvBatch& b, int mode, bool ds, int nb, int N, int rpc, cudaStream_t s,
+                    long long* launches);
+// rows per chunk for njobs windows (256 to 1024, a multiple of 8)
 int sv_rows_per_chunk(int N, int njobs);
+// Chunk sums.  mode 0: C[e] = sum of entry e < ncols * nb, added into
+// H[(e / nb) * ldh + e % nb] when H is set.  mode 1: the Gram matrix G = w^H w
+// of the block: R1 = chol(G) (upper, G = R1^H R1), r[0..nb^2) = R1^-1 and
+// r[4..4+nb^2) = R1 (nb = 1: H[0] = ||w||).  mode 2 (nb = 2, the second
+// Cholesky-QR pass): R2 = chol(G), r[0..4) = R2^-1, H[a * ldh + b] = (R2 R1)[a][b].
+// A block whose Cholesky factor has a relative pivot below 1e-14 sets r[8] = 1.
 struct SvReduceJob {
   const double2* part;
-  int ldp, nchunks, ncols;
-  int mode;      // 0: C = sum (H[i * ldh] += sum if H); 1: beta = sqrt(sum), H[0] = beta, invb = 1/beta
+  int ldp, nchunks, ncols, nb;
+  int mode;
   double2* C;
   double2* H;
   int ldh;
-  double* invb;
+  double2* r;
 };
 struct SvReduceBatch {
   int n;
   SvReduceJob job[kMaxBatch];
 };
 void launch_sv_reduce(const SvReduceBatch& b, cudaStream_t s, long long* launches);
+// dst1[:, b] (and dst2[:, b]) = sum_a w[:, a] r[a * nb + b] for b < nb (in place allowed)
 struct SvNormJob {
   const void* w;
   int ldw;
@@ -314,13 +324,13 @@ struct SvNormJob {
   int ld1;
   void* dst2;  // may be NULL
   int ld2;
-  const double* invb;
+  const double2* r;
 };
 struct SvNormBatch {
   int n;
   SvNormJob job[kMaxBatch];
 };
-void launch_sv_normalize(const SvNormBatch& b, bool ds, int N, cudaStream_t s, long long* launches);
+void launch_sv_normalize(const SvNormBatch& b, bool ds, int nb, int N, cudaStream_t s, long long* launches);
 // Q[:, 0:k] = Q[:, 0:m] Z32 in place (FP32), Z32 [m][ldz] complex64
 void launch_c64_rotate_inplace(float2* Q, int ldq, int N, int m, const float2* Z32, int ldz, int k, cudaStream_t s,
                                long long* launches);

@@ -272,7 +272,8 @@ def test_reduced_copies(swi, name, shape):
 
 
 # --------------------------------------------------------------------------- single-vector windows
-def _solve_sv(swi, w, n_r, p, prec=None, rel_tol=REL_TOL_DS, inflate=1.3, extra=4, counts=None, budget=100000):
+def _solve_sv(swi, w, n_r, p, prec=None, rel_tol=REL_TOL_DS, inflate=1.3, extra=4, counts=None, budget=100000,
+              block=1):
     A = _dense(w)
     eps_o, U_o = eigen.dense_spectrum(A)
     counts = partition.window_counts(n_r, p) if counts is None else counts
@@ -282,31 +283,57 @@ def _solve_sv(swi, w, n_r, p, prec=None, rel_tol=REL_TOL_DS, inflate=1.3, extra=
         c.set_potential(w.V)
         c.set_absorber(w.gamma_L, w.gamma_R)
         c.set_windows(sig, req)
-        info = c.solve(block=1, rel_tol=rel_tol, n_keep=n_r, max_matvecs=budget)
+        info = c.solve(block=block, rel_tol=rel_tol, n_keep=n_r, max_matvecs=budget)
         eps, U = c.eigenpairs()
         res = c.residuals()
         winfo = c.window_info()
     return eps_o, U_o, eps, U, res, info, winfo
 
 
-def test_single_vector_windows_small(swi):
+@pytest.mark.parametrize("block", [1, 2])
+def test_single_vector_windows_small(swi, block):
     # block width 1: the paper's single-vector restarted Arnoldi per window,
-    # complex128 bases with double-single products
+    # complex128 bases with double-single products; block width 2: the same
+    # loop adding two vectors per window and step
     w = W.make_wire(8, 8, 14, 0.5, 4, 1)
-    eps_o, U_o, eps, U, res, info, winfo = _solve_sv(swi, w, 16, 2)
+    eps_o, U_o, eps, U, res, info, winfo = _solve_sv(swi, w, 16, 2, block=block)
     _check_pairs(w, eps_o, U_o, eps, U, res, info, 16, RES_TOL_DS)
     assert info["n_duplicates"] > 0 and info["n_holes"] == 0
 
 
-def test_single_vector_windows_ragged_many(swi):
+@pytest.mark.parametrize("block", [1, 2])
+def test_single_vector_windows_ragged_many(swi, block):
     # ragged grid, 5 windows of uneven requests (more windows than a CTA's
     # 4-column stencil group, a ragged last group)
     w = W.make_wire(11, 9, 17, 0.5, 5, 7)
-    eps_o, U_o, eps, U, res, info, winfo = _solve_sv(swi, w, 30, 5, inflate=1.6, extra=6)
+    eps_o, U_o, eps, U, res, info, winfo = _solve_sv(swi, w, 30, 5, inflate=1.6, extra=6, block=block)
     _check_pairs(w, eps_o, U_o, eps, U, res, info, 30, RES_TOL_DS)
 
 
-def test_single_vector_interior_window_bench_rule(swi):
+def test_two_vector_blocks_find_degenerate_partners(swi):
+    # a square cross-section with the wells on the axis: the x <-> y mirror
+    # makes many eigenvalues exactly twofold (15 of the lowest 60 here).  With
+    # 2-vector blocks every window must return both vectors of each pair, and
+    # the pair's projector must match the dense one.
+    w = W.make_wire(10, 10, 20, 0.5, 6, 1)
+    A = _dense(w)
+    eps_o, U_o = eigen.dense_spectrum(A)
+    n_r = 48
+    degen = [i for i in range(n_r - 1) if abs(eps_o[i + 1] - eps_o[i]) <= 1e-9 * max(1.0, abs(eps_o[i]))]
+    assert len(degen) >= 8
+    eps_o2, U_o2, eps, U, res, info, winfo = _solve_sv(swi, w, n_r, 4, block=2)
+    _check_pairs(w, eps_o, U_o, eps, U, res, info, n_r, RES_TOL_DS)
+    for i in degen:
+        if i + 1 >= n_r:
+            continue
+        idx = [int(k) for k in np.argsort(np.abs(eps - eps_o[i]))[:2]]
+        P = eigen.cluster_projector(U, idx)
+        Po = eigen.cluster_projector(U_o, [i, i + 1])
+        assert np.max(np.abs(P - Po)) <= 1e-8 * max(1.0, np.max(np.abs(Po)))
+
+
+@pytest.mark.parametrize("block", [1, 2])
+def test_single_vector_interior_window_bench_rule(swi, block):
     # a reduced copy of the 48x48x96 workload (same recipe and seed), windows
     # cut by the bench's rule (equal counts, shift mid-run, requests x1.25 + 4);
     # the interior window 3 of 4 against the dense spectrum
@@ -319,7 +346,7 @@ def test_single_vector_interior_window_bench_rule(swi):
     lo, hi = j * (n_r // p), (j + 1) * (n_r // p)
     with _ctx(swi, w) as c:
         c.set_windows(sig[j:j + 1], req[j:j + 1])
-        info = c.solve(block=1, rel_tol=REL_TOL_DS, n_keep=0, max_matvecs=200000)
+        info = c.solve(block=block, rel_tol=REL_TOL_DS, n_keep=0, max_matvecs=200000)
         eps, U = c.eigenpairs()
         res = c.residuals()
     assert info["status"] == "SWI_OK", info
@@ -340,13 +367,15 @@ def test_single_vector_interior_window_bench_rule(swi):
         assert np.max(np.abs(P - Po)) <= 1e-8 * max(1.0, np.max(np.abs(Po)))
 
 
-def test_precision_form_small(swi):
+@pytest.mark.parametrize("block", [1, 2])
+def test_precision_form_small(swi, block):
     # SWI_PREC_MIXED: complex64 Krylov vectors and FP32 products; the pairs
     # carry FP32-class errors, which the solve reports through its explicit
     # FP64 residuals.  Stated bounds: eigenvalues within 2e-6 max(1, |eps|)
     # of the dense FP64 spectrum, explicit relative residuals below 1e-6.
     w = W.make_wire(8, 8, 14, 0.5, 4, 1)
-    eps_o, U_o, eps, U, res, info, winfo = _solve_sv(swi, w, 16, 2, prec=swi.PREC_MIXED, rel_tol=1e-6)
+    eps_o, U_o, eps, U, res, info, winfo = _solve_sv(swi, w, 16, 2, prec=swi.PREC_MIXED, rel_tol=1e-6,
+                                                     block=block)
     assert len(eps) == 16, info
     assert _eps_err(eps, eps_o[:16]) <= 2e-6, _eps_err(eps, eps_o[:16])
     assert np.max(res) <= 1e-6, np.max(res)
@@ -655,3 +684,89 @@ def test_transmission_function_autograd(swi):
         Em[e] -= d
         fd = (loss_direct(w.V, Ep) - loss_direct(w.V, Em)) / (2 * d)
         assert abs(dE[e] - fd) <= 1e-6 * max(1.0, abs(fd)), (e, dE[e], fd)
+
+
+# --------------------------------------------------------------------------- continuation, holes
+def _sv_ctx(swi, w):
+    c = swi.Context(w.nx, w.ny, w.nz, w.h)
+    c.set_potential(w.V)
+    c.set_absorber(w.gamma_L, w.gamma_R)
+    return c
+
+
+def test_continuation_and_checkpoint_resume(swi):
+    # the lowest 12 pairs in two windows, then one window above added as a
+    # continuation run (the old pairs kept, Algorithm 2 over the union): the
+    # lowest 20 match the dense spectrum.  The same continuation from pairs
+    # restored into a fresh context (a checkpoint) gives the same set.
+    w = W.make_wire(8, 8, 14, 0.5, 4, 1)
+    A = _dense(w)
+    eps_o, U_o = eigen.dense_spectrum(A)
+    sig, req = W.count_windows(eps_o.real[:12], [6, 6], inflate=1.3, extra=4)
+    sig2, req2 = W.count_windows(eps_o.real[10:26], [16], inflate=1.3, extra=4)
+    with _sv_ctx(swi, w) as c:
+        c.set_windows(sig, req)
+        c.solve(block=1, rel_tol=REL_TOL_DS, n_keep=0, max_matvecs=40000)
+        e1, U1 = c.eigenpairs()
+        info = c.solve_more(sig2, req2, block=1, rel_tol=REL_TOL_DS, n_keep=20, max_matvecs=40000)
+        eps, U = c.eigenpairs()
+        res = c.residuals()
+        s_all, holes = c.windows()
+    assert info["status"] == "SWI_OK", info
+    assert len(s_all) == 3 and np.all(np.diff(s_all) > 0) and not holes.any()
+    assert _eps_err(eps, eps_o[:20]) <= EPS_TOL and np.max(res) <= RES_TOL_DS
+    _check_utu(w, eps, U, res)
+    with _sv_ctx(swi, w) as c:
+        c.set_eigenpairs(e1, U1)
+        info = c.solve_more(sig2, req2, block=1, rel_tol=REL_TOL_DS, n_keep=20, max_matvecs=40000)
+        eps_r = c.eigenvalues()
+    assert info["status"] in ("SWI_OK", "SWI_HOLES"), info
+    assert _eps_err(eps_r, eps_o[:20]) <= EPS_TOL
+
+
+def test_fill_holes(swi):
+    # two windows with a gap between them (the lowest 8 and pairs 16..23, each
+    # requested exactly): the merge finds no redundancy across the interface;
+    # Algorithm 1's hole loop inserts a window in the gap until the lowest 24
+    # are complete and no hole remains
+    w = W.make_wire(8, 8, 14, 0.5, 4, 1)
+    A = _dense(w)
+    eps_o, U_o = eigen.dense_spectrum(A)
+    r = eps_o.real
+    sig = np.array([0.5 * (r[0] + r[7]), 0.5 * (r[16] + r[23])])
+    with _sv_ctx(swi, w) as c:
+        c.set_windows(sig, [8, 8])
+        info0 = c.solve(block=1, rel_tol=REL_TOL_DS, n_keep=0, max_matvecs=40000)
+        s0, h0 = c.windows()
+        assert h0[0] == 1 and info0["n_holes"] == 1, (info0, h0)
+        info = c.fill_holes(r.min(), r.max(), max_rounds=4, block=1, rel_tol=REL_TOL_DS, n_keep=24,
+                            max_matvecs=40000)
+        eps, U = c.eigenpairs()
+        res = c.residuals()
+        s1, h1 = c.windows()
+    assert info["windows_added"] >= 1 and info["status"] == "SWI_OK", info
+    assert s1[0] == s0[0] and s1[-1] == s0[-1] and np.all((s1[1:-1] > s0[0]) & (s1[1:-1] < s0[1]))
+    assert not h1.any()
+    assert _eps_err(eps, eps_o[:24]) <= EPS_TOL and np.max(res) <= RES_TOL_DS
+
+
+def test_plan_windows_sampled(swi):
+    # the planner without foreknowledge (Section 2.2.1): exterior solves give
+    # E_min and E_max, sampling solves march up the spectrum; its windows match
+    # the oracle's placement on the dense spectrum (runs of equal counts, shift
+    # mid-run, requests x1.25 + 4), and solving them gives the lowest n_r pairs
+    w = W.config_wire("wire_10x10x20")
+    A = _dense(w)
+    eps_o, U_o = eigen.dense_spectrum(A)
+    n_r, p = 48, 4
+    sig_o, req_o = W.count_windows(eps_o.real[:n_r], [n_r // p] * p, inflate=1.25, extra=4)
+    with _sv_ctx(swi, w) as c:
+        sig, req, pinfo = c.plan_windows_sampled(n_r, p, sample_tol=1e-8)
+        assert abs(pinfo["e_min"] - eps_o.real.min()) <= 1e-6
+        assert abs(pinfo["e_max"] - eps_o.real.max()) <= 1e-6 * max(1.0, abs(eps_o.real.max()))
+        np.testing.assert_array_equal(req, req_o)
+        np.testing.assert_allclose(sig, sig_o, atol=1e-6)
+        info = c.solve(block=1, rel_tol=REL_TOL_DS, n_keep=n_r, max_matvecs=60000)
+        eps = c.eigenvalues()
+    assert info["status"] == "SWI_OK", info
+    assert _eps_err(eps, eps_o[:n_r]) <= EPS_TOL

@@ -3,16 +3,20 @@
 
 One step = one pass of the whole hot path over the 48x48x96 wire (N = 221,184,
 24 seeded wells, Gaussian absorbers): solve the 400 lowest-real-part pairs in 8
-windows of equal eigenpair count, each a single-vector Krylov-Schur iteration
-on the shifted, never-inverted operator with SM selection (the paper's
-implicitly restarted Arnoldi form, all windows batched into shared stencil and
-Gram-Schmidt launches), merge them with Algorithm 2, keep the 400 lowest with
-U^T U = I, verify every residual explicitly in FP64, then T(E) at 128 energies
-and the adjoint dL/dV, dL/dE.  Complex128 vectors; the stencil, the
-Gram-Schmidt products, the restart rotations and the projected Schur steps run
-in double-single arithmetic (a float head and tail, ~2^-46 relative per term)
-on the FP32 pipes, the explicit residual check in native FP64.  Metric:
-converged eigenpairs (explicit relative residual <= 1e-8) per second.
+windows of equal eigenpair count, each a Krylov-Schur iteration on the
+shifted, never-inverted operator with SM selection (the exact-shift restart of
+the paper's implicitly restarted Arnoldi method) adding 2 vectors per step --
+the wire's square cross-section makes about a quarter of its eigenvalues
+exactly twofold, and a single starting vector finds only one vector of each
+such pair -- with all windows batched into shared stencil and Gram-Schmidt
+launches; merge them with Algorithm 2, keep the 400 lowest with U^T U = I,
+verify every residual explicitly in FP64, then T(E) at 128 energies and the
+adjoint dL/dV, dL/dE.  Complex128 basis vectors; the stencil, the accurate
+Gram-Schmidt pass and update, the restart rotations and the projected Schur
+steps run in double-single arithmetic (a float head and tail, ~2^-46 relative
+per term) on the FP32 pipes, the first Gram pass and the small second update
+in FP32, the explicit residual check in native FP64.  Metric: converged
+eigenpairs (explicit relative residual <= 1e-8) per second.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--no-cpu-baseline] [--no-extras] [--matvec-budget M] [--windows P]
@@ -49,10 +53,13 @@ REL_TOL = 1e-8
 # converged within it deliver what they have; only pairs whose explicit FP64
 # residual is <= REL_TOL are counted.
 MATVEC_BUDGET = 150000
-# Block width of the windows: single-vector (the form of the paper's ARPACK
-# solver).  Block width 16 converged none of an interior window's 67 pairs in
-# 16,384 applications where single-vector windows converged 19 in 8,192.
-BLOCK = 1
+# Block width of the windows: 2 vectors per step.  Block width 16 converged
+# none of an interior window's 67 pairs in 16,384 applications where
+# single-vector windows converged 19 in 8,192; single-vector windows miss one
+# vector of each twofold eigenvalue (338 of 400 pairs in 860 s).
+BLOCK = 2
+# window requests: ceil(INFLATE x run length) + EXTRA
+INFLATE, EXTRA = 1.1, 2
 # FP64 peak of GB300 derived from unit counts and clocks: 152 SMs x 2 FP64 FMA
 # per SM clock x 2 flops x the sampled SM clock (nominal 1.25 TFLOP/s at 2.07 GHz).
 FP64_FLOPS_PER_CLK = 152 * 2 * 2
@@ -109,11 +116,13 @@ def plan(cfg, ctx=None, wire=None):
         lam = march_spectrum(ctx, wire, n_r + 20)
         source = "gpu_march"
     # "8 equal-width windows" read as 8 windows of equal eigenpair count (runs of
-    # n_r/p consecutive real parts, shift at the middle of each run, requests
-    # x1.25 + 4): equal widths in energy would put 357 of the 400 pairs of this
-    # spectrum into the top window.
+    # n_r/p consecutive real parts, shift at the middle of each run): equal
+    # widths in energy would put 357 of the 400 pairs of this spectrum into the
+    # top window.  Requests x1.1 + 2 leave a few redundant pairs at each
+    # interface (Section 2.2.2); an interface left without one is a hole, which
+    # the step fills (Algorithm 1).
     per = n_r // cfg["p"]
-    sig, req = W.count_windows(lam[:n_r], [per] * cfg["p"], inflate=1.25, extra=4)
+    sig, req = W.count_windows(lam[:n_r], [per] * cfg["p"], inflate=INFLATE, extra=EXTRA)
     E = W.energy_grid(lam[0], lam[n_r - 1], cfg["n_E"])
     return sig, req, E, source
 
@@ -311,10 +320,12 @@ def refine_sweep(ctx):
                     "largest residual falls; not part of the timed step"}
 
 
-def precision_form(swi, stream, wire, sig, req, n_r, budget, eps64):
-    """The reduced-precision form (complex64 Krylov vectors, FP32 stencil and products) on the same
-    workload and windows: time, pairs, and the error of its eigenvalues and residuals against the
-    FP64 run of the timed step (pairs matched by nearest eigenvalue)."""
+def precision_form(swi, stream, wire, sig, req, n_r, budget, eps64, E, T64):
+    """The reduced-precision form on the same workload and windows: complex64 Krylov vectors with
+    FP32 stencil and products, the pairs widened to complex128, then FP64 residual-correction
+    sweeps (Rayleigh-Ritz on span[U_g, R_u]).  Reported: time, pairs, residuals, and the error of
+    eigenvalues and T(E) against the FP64 run of the timed step (pairs matched by nearest
+    eigenvalue), before and after the sweeps."""
     import torch
     ctx = swi.Context(wire.nx, wire.ny, wire.nz, wire.h, precision=swi.PREC_MIXED, stream=stream.cuda_stream)
     ctx.set_potential(wire.V)
@@ -322,22 +333,46 @@ def precision_form(swi, stream, wire, sig, req, n_r, budget, eps64):
     ctx.set_windows(sig, req)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    info = ctx.solve(block=1, rel_tol=1e-6, n_keep=n_r, max_matvecs=budget)
+    try:
+        info = ctx.solve(block=BLOCK, rel_tol=1e-6, n_keep=n_r, max_matvecs=budget)
+    except RuntimeError as e:  # a status other than OK still leaves the pairs in the context
+        info = {"status": str(e), "n_pairs": len(ctx.eigenvalues()), "matvecs": -1}
     torch.cuda.synchronize()
-    t = time.perf_counter() - t0
-    eps = ctx.eigenvalues()
-    res = ctx.residuals()
+    t_solve = time.perf_counter() - t0
+
+    def errors():
+        eps = ctx.eigenvalues()
+        res = ctx.residuals()
+        d = np.abs(eps[:, None] - eps64[None, :])
+        err = np.min(d, axis=1) / np.maximum(1.0, np.abs(eps))
+        T = ctx.transmission(E)
+        return eps, res, err, T
+
+    eps, res, err, T = errors()
+    before = {"rel_res_quantiles_10_50_90_max": [float(x) for x in np.quantile(res, [0.1, 0.5, 0.9, 1.0])],
+              "eig_err_vs_fp64_median_max": [float(np.median(err)), float(np.max(err))],
+              "T_abs_err_vs_fp64_max": float(np.max(np.abs(T - T64))), "pairs_rel_res_le_1e-6": int(np.sum(res <= 1e-6))}
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    try:
+        rinfo = ctx.refine(max_sweeps=2, group=16, rel_tol=REL_TOL)
+    except RuntimeError as e:
+        rinfo = {"status": str(e)}
+    torch.cuda.synchronize()
+    t_ref = time.perf_counter() - t1
+    eps, res, err, T = errors()
+    after = {"rel_res_quantiles_10_50_90_max": [float(x) for x in np.quantile(res, [0.1, 0.5, 0.9, 1.0])],
+             "eig_err_vs_fp64_median_max": [float(np.median(err)), float(np.max(err))],
+             "T_abs_err_vs_fp64_max": float(np.max(np.abs(T - T64))), "pairs_rel_res_le_1e-6": int(np.sum(res <= 1e-6)),
+             "pairs_rel_res_le_1e-8": int(np.sum(res <= 1e-8)), "sweep_status": rinfo.get("status")}
     ctx.close()
-    d = np.abs(eps[:, None] - eps64[None, :])
-    err = np.min(d, axis=1) / np.maximum(1.0, np.abs(eps))
-    n6 = int(np.sum(res <= 1e-6))
-    return {"seconds": round(t, 2), "status": info["status"], "pairs": int(info["n_pairs"]),
-            "pairs_rel_res_le_1e-6": n6, "pairs_per_s_at_1e-6": n6 / t,
-            "pairs_rel_res_le_1e-8": int(np.sum(res <= 1e-8)), "matvecs": int(info["matvecs"]),
-            "rel_res_quantiles_10_50_90_max": [float(x) for x in np.quantile(res, [0.1, 0.5, 0.9, 1.0])],
-            "eig_err_vs_fp64_median_max": [float(np.median(err)), float(np.max(err))],
+    n6 = after["pairs_rel_res_le_1e-6"]
+    return {"seconds_solve": round(t_solve, 2), "seconds_sweeps": round(t_ref, 2), "status": info["status"],
+            "pairs": int(info["n_pairs"]), "matvecs": int(info["matvecs"]),
+            "pairs_per_s_at_1e-6": n6 / (t_solve + t_ref), "before_sweeps": before, "after_2_sweeps": after,
             "note": "complex64 Krylov vectors, FP32 stencil (tensor-map staged) and Gram-Schmidt products with "
-                    "FP64 chunk sums, double-single projected eigenproblems; not part of the timed step"}
+                    "FP64 chunk sums, double-single projected eigenproblems; then two FP64 correction sweeps; "
+                    "errors against the FP64 step's pairs and T(E); not part of the timed step"}
 
 
 def single_window(swi, stream, wire, lam, n_r, budget):
@@ -421,8 +456,24 @@ def main():
 
     log(f"plan ({plan_source}, {t_plan:.1f} s): sigma {np.round(sig, 4).tolist()} n_req {list(map(int, req))}")
 
+    e_lo, e_hi = float(sig[0]) - 1.0, None
+
+    def solve_fill(c):
+        """Algorithm 1 on the planned windows: solve, merge, and insert windows in holes."""
+        nonlocal e_hi
+        info = c.solve(block=BLOCK, rel_tol=REL_TOL, n_keep=n_keep, max_matvecs=budget)
+        info["holes_filled"] = 0
+        if info["n_holes"] > 0:
+            e_hi = info["anorm"] if e_hi is None else e_hi
+            mv = info["matvecs"]
+            info = c.fill_holes(e_lo, e_hi, max_rounds=2, block=BLOCK, rel_tol=REL_TOL, n_keep=n_keep,
+                                max_matvecs=budget)
+            info["matvecs"] += mv
+            info["holes_filled"] = info.pop("windows_added")
+        return info
+
     def step():
-        info = ctx.solve(block=BLOCK, rel_tol=REL_TOL, n_keep=n_keep, max_matvecs=budget)
+        info = solve_fill(ctx)
         ctx.transmission(E)
         ctx.grad(E, dLdT)
         return info
@@ -439,7 +490,7 @@ def main():
     ctx2.set_potential(wire.V)
     ctx2.set_absorber(wire.gamma_L, wire.gamma_R)
     ctx2.set_windows(sig, req)
-    info_e = ctx2.solve(block=BLOCK, rel_tol=REL_TOL, n_keep=n_keep, max_matvecs=budget)
+    info_e = solve_fill(ctx2)
     ctx2.transmission(E)
     dV, dE = ctx2.grad(E, dLdT)
     eps_host = ctx2.eigenvalues()
@@ -516,28 +567,31 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * elapsed_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64 (complex128 vectors; double-single stencil, Gram-Schmidt products, rotations and Schur "
-                 "steps; native FP64 residual check)",
+        "dtype": "f64 (complex128 basis; double-single stencil, accurate Gram-Schmidt pass, rotations and "
+                 "Schur steps; FP32 first Gram pass and second update; native FP64 residual check)",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "grid": [wire.nx, wire.ny, wire.nz], "N": wire.N, "n_r": n_r,
                    "windows": len(sig), "block": BLOCK, "n_E": len(E), "rel_tol": REL_TOL,
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "windows_from": plan_source, "plan_s": round(t_plan, 2),
-                   "window_rule": "equal eigenpair count (n_r/p per window), shift mid-run, requests x1.25+4",
+                   "window_rule": f"equal eigenpair count (n_r/p per window), shift mid-run, requests "
+                                  f"x{INFLATE}+{EXTRA}; holes filled by Algorithm 1's loop",
                    "matvec_budget_per_window": budget,
                    "sigma": [round(float(x), 5) for x in sig], "n_req": [int(x) for x in req],
                    "per_window": [{"n_conv": x["n_conv"], "matvecs": x["matvecs"], "restarts": x["restarts"],
                                    "basis": x["basis"]} for x in winfo],
-                   "arith": "complex128 Krylov vectors; stencil, Gram-Schmidt products (classical, twice), restart "
-                            "rotations and the projected Schur steps in double-single (2 x FP32) arithmetic; the "
-                            "explicit residual check of every delivered pair in native FP64",
+                   "arith": "complex128 Krylov basis; classical Gram-Schmidt twice as three passes over each basis: "
+                            "Gram in FP32, update plus second Gram in double-single (2 x FP32), second update (by "
+                            "the small second-pass coefficients) in FP32 with the new vector kept in double-single; "
+                            "stencil, Cholesky-QR of the 2-vector blocks, restart rotations and the projected Schur "
+                            "steps in double-single; the explicit residual check of every delivered pair in native FP64",
                    "l2": "inputs larger than L2 (Krylov bases ~6.5 GB per solve)"},
         "roofline": roof,
         "kernels": breakdown,
         "schur_side_streams": {"launches": prof["schur"]["launches"], "ms_total": prof["schur"]["ms"],
                                "note": "one CTA per window restart on the window's own stream, overlapped "
                                        "with the other windows' expansion"},
-        "solve": {k: last[k] for k in ("n_pairs", "n_converged", "n_duplicates", "n_holes", "matvecs",
+        "solve": {k: last[k] for k in ("n_pairs", "n_converged", "n_duplicates", "n_holes", "holes_filled", "matvecs",
                                        "max_rel_res", "t_krylov_s", "t_merge_s", "status")},
         "e2e": {"value": info_e["n_converged"] * world / te, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "seconds": te},
@@ -549,9 +603,10 @@ def main():
     out["stencil_c64"] = stencil_c64_rate(swi, stream, hbm)
     if not args.no_extras:
         eps64 = ctx.eigenvalues()
+        T64 = ctx.transmission(E)
         log("precision form")
         try:
-            out["precision_form"] = precision_form(swi, stream, wire, sig, req, n_r, budget, eps64)
+            out["precision_form"] = precision_form(swi, stream, wire, sig, req, n_r, budget, eps64, E, T64)
         except RuntimeError as e:
             out["precision_form"] = {"error": str(e)}
         log("single window")

@@ -85,7 +85,7 @@ typedef struct {
                            up to b, j the window index: the stagger keeps
                            equal windows from restarting in step; for
                            b = 1 or 2 max(2 n_req + 1,
-                           keep + b (128 + 8 (j mod 3))), at most 1000 for
+                           keep + 128 + 8 (j mod 3)), at most 1000 for
                            b = 1 and 510 for b = 2) */
   int keep;             /* Ritz vectors kept at a restart (default
                            max(n_req + ceil(n_req/2), n_req + b), at most
@@ -428,6 +428,23 @@ swi_status swi_profile_read(swi_ctx* ctx, swi_kernel_stats* out);
  * E, T_out: host arrays of nE doubles.  Errors: SWI_ESTATE (no pairs or no
  * absorbers), SWI_EINVAL (sizes, NULL, non-finite energy), SWI_ECUDA. */
 swi_status swi_transmission_noalloc(swi_ctx* ctx, int nE, const double* E, double* T_out);
+
+/* Self-check of the projected eigenproblem of a thick restart (Section 2.1:
+ * the exact-shift restart of the implicitly restarted Arnoldi method, which
+ * the solver computes on the device once per restart of every window): the
+ * complex Schur form H Z = Z T of an m x m matrix H, the `keep` Ritz values
+ * of smallest magnitude moved to the leading block, with b coupling rows B
+ * (the rows below H of the Arnoldi relation).  For tests of that kernel
+ * against a host eigensolver; it touches no state of ctx but its stream.
+ * H: m*m complex128 (interleaved re, im), row-major, host.  B: b*m complex128
+ * row-major, host (b = 1 or 2; NULL: zero rows).  arith: SWI_ARITH_DS (the
+ * solver's double-single kernel) or SWI_ARITH_F64.  T_out, Z_out: m*m complex128
+ * row-major host arrays (T upper triangular, Z unitary, column i = Schur
+ * vector i).  info_out[4]: kept columns, -, QR status (0 converged, 1
+ * iteration limit, 3 m too large), Givens updates / 1024.  Errors: SWI_EINVAL
+ * (m outside 2..1024, b, keep outside 1..m-b, NULL), SWI_ECUDA. */
+swi_status swi_check_schur(swi_ctx* ctx, int m, int b, int keep, const double* H, const double* B, int arith,
+                           double* T_out, double* Z_out, int* info_out);
 
 /* Message of the last failing call on ctx (thread-local for ctx == NULL). */
 const char* swi_last_error(const swi_ctx* ctx);

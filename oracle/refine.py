@@ -22,11 +22,14 @@ fixes a reading:
   its eigenvalue error is quadratic in the vectors' error, where the Hermitian
   projection Q^H A Q of a non-Hermitian A gives a linear one.  The result does
   not depend on which basis of the span is used;
-* a group keeps its Rayleigh-Ritz pairs only if their largest relative
-  residual is below the group's previous largest; otherwise its previous pairs
-  stay (far from convergence the SM selection around sigma_g can pick
-  directions with larger residuals: the sweep sharpens pairs, it is not a
-  solver);
+* a group keeps its Rayleigh-Ritz pairs unless they lower the number of the
+  group's pairs at rel_tol or raise its largest relative residual more than
+  tenfold; otherwise its previous pairs stay.  The sweep sharpens eigenvalues
+  quadratically while a residual can stay level or rise a little (a vector
+  error spread over all directions is not removed by one residual direction),
+  so a rule on the residual alone would discard exactly those gains; far from
+  convergence, though, the SM selection around sigma_g can pick directions
+  away from pairs that had converged;
 * all pairs then pass Algorithm 2 as one window (equal-eigenvalue projection,
   redundancy drop, v^T v = 1) and are ordered by real part.
 """
@@ -40,7 +43,7 @@ from . import eigen, partition
 def rr_sweep(apply_A, eps: np.ndarray, U: np.ndarray, res: np.ndarray, rel_tol: float, group: int = 16,
              eq_rtol: float = 1e-8, drop_tol: float = 1e-6, anorm: float | None = None):
     """One sweep over the Re-sorted pairs (eps, U) with relative residuals res (relative to anorm;
-    anorm None skips the keep-only-if-better rule)."""
+    anorm None skips the rule that keeps a group's previous pairs)."""
     n = len(eps)
     eps_new = np.array(eps, dtype=np.complex128, copy=True)
     U_new = np.array(U, dtype=np.complex128, copy=True)
@@ -57,8 +60,11 @@ def rr_sweep(apply_A, eps: np.ndarray, U: np.ndarray, res: np.ndarray, rel_tol: 
         theta, Y = np.linalg.eig(np.linalg.solve(S, K))
         sel = np.argsort(np.abs(theta), kind="stable")[:len(g)]
         e, V = eigen.sort_by_real(theta[sel] + sigma, Q @ Y[:, sel])
-        if anorm is not None and not np.max(eigen.residual_norms(apply_A, e, V) / anorm) < np.max(res[g]):
-            continue
+        if anorm is not None:
+            r_new = eigen.residual_norms(apply_A, e, V) / anorm
+            r_old = res[g]
+            if np.sum(r_new <= rel_tol) < np.sum(r_old <= rel_tol) or np.max(r_new) > 10.0 * np.max(r_old):
+                continue
         eps_new[g] = e
         U_new[:, g] = V
     eps2, U2, _, _ = partition.combine([eps_new], [U_new], eq_rtol, drop_tol)

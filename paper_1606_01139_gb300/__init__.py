@@ -29,7 +29,8 @@ EXPORTS = ("swi_create", "swi_set_potential", "swi_set_absorber", "swi_set_windo
            "swi_apply", "swi_apply_ds", "swi_apply_c64", "swi_solve", "swi_solve_more", "swi_fill_holes",
            "swi_get_windows", "swi_refine", "swi_get_window_info", "swi_get_eigenpairs", "swi_copy_eigenpairs",
            "swi_set_eigenpairs", "swi_residuals", "swi_transmission", "swi_grad", "swi_profile",
-           "swi_profile_read", "swi_transmission_noalloc", "swi_last_error", "swi_launch_count", "swi_destroy")
+           "swi_profile_read", "swi_transmission_noalloc", "swi_check_schur", "swi_last_error", "swi_launch_count",
+           "swi_destroy")
 
 KERNEL_CLASSES = ("stencil", "gram", "update", "cholqr", "schur", "rotate", "merge", "proj", "trans", "grad")
 
@@ -123,6 +124,7 @@ def load(path: str = LIB_PATH):
         "swi_grad": (I, [VP, I, VP, VP, VP, I, VP]),
         "swi_profile": (I, [VP, I]),
         "swi_transmission_noalloc": (I, [VP, I, VP, VP]),
+        "swi_check_schur": (I, [VP, I, I, I, VP, VP, I, VP, VP, VP]),
         "swi_profile_read": (I, [VP, P(KernelStats)]),
         "swi_last_error": (C.c_char_p, [VP]),
         "swi_launch_count": (C.c_longlong, [VP]),
@@ -392,14 +394,29 @@ class Context:
     def transmission_noalloc(self, E):
         """T(E) through swi_transmission_noalloc: no device allocation during the call.
 
-        For callers that cannot allocate at call time (stream capture, a
-        framework that owns the memory budget); at most 64 pairs and 1024
+        For callers that must not allocate device memory while it runs (a host
+        framework that owns the whole memory budget); at most 64 pairs and 1024
         energies, and calls must not overlap on the GPU (shared scratch).
         """
         E = _c_arr(np.atleast_1d(E), np.float64)
         T = np.empty_like(E)
         self._check(self._lib.swi_transmission_noalloc(self._h, len(E), _ptr(E), _ptr(T)))
         return T
+
+    def check_schur(self, H, B=None, keep=None, arith=ARITH_DS):
+        """The device's thick-restart Schur step on a host matrix H (m x m): (T, Z, info) with
+        H Z = Z T, the `keep` Ritz values of smallest magnitude first; info = (kept, -, status, work)."""
+        H = _c_arr(np.asarray(H), np.complex128)
+        m = H.shape[0]
+        b = 1 if B is None else np.atleast_2d(B).shape[0]
+        Bc = None if B is None else _c_arr(np.atleast_2d(B), np.complex128)
+        keep = m // 2 if keep is None else int(keep)
+        T = np.empty((m, m), np.complex128)
+        Z = np.empty((m, m), np.complex128)
+        info = np.zeros(4, np.int32)
+        self._check(self._lib.swi_check_schur(self._h, m, b, keep, _ptr(H), None if Bc is None else _ptr(Bc), int(arith),
+                                              _ptr(T), _ptr(Z), _ptr(info)))
+        return T, Z, info
 
     def grad(self, E, dLdT, dLdV_out=None):
         """(dL/dV[N], dL/dE[nE]) for the weights dL/dT (dL/dE_e = dLdT_e dT_e/dE_e).

@@ -890,9 +890,11 @@ swi_status do_refine(swi_ctx* c, const swi_refine_opts* o, swi_refine_info* info
       if (si[gi] != 0) return fail(c, SWI_ENOCONV, "refine: singular Q^T Q in a group");
       if (oi[4 * gi + 2] != 0) return fail(c, SWI_ENOCONV, "refine: a projected eigenproblem did not converge");
     }
-    // a group is replaced only if its largest explicit residual falls; otherwise
-    // its previous pairs are put back (a sweep sharpens eigenvalues, it is not a
-    // solver: on pairs far from convergence it can raise the residual)
+    // a group's Rayleigh-Ritz pairs replace its previous ones unless they
+    // lower the number of the group's pairs at rel_tol or raise its largest
+    // explicit residual more than tenfold (a sweep sharpens eigenvalues, which
+    // a residual need not show; far from convergence, though, it can move
+    // pairs away from converged ones)
     {
       std::vector<double> rn;
       explicit_residuals(c, Unew.as<double2>(), n, epsnew.as<double2>(), n, rn);
@@ -901,11 +903,14 @@ swi_status do_refine(swi_ctx* c, const swi_refine_opts* o, swi_refine_info* info
         const int lo = gi * g, ng = std::min(g, n - lo);
         if (ioff[gi + 1] == ioff[gi]) continue;
         double before = 0.0, after = 0.0;
+        int conv_before = 0, conv_after = 0;
         for (int k = lo; k < lo + ng; ++k) {
           before = std::max(before, c->resid[k]);
           after = std::max(after, rn[k]);
+          conv_before += c->resid[k] <= rel_tol;
+          conv_after += rn[k] <= rel_tol;
         }
-        if (after < before) continue;
+        if (conv_after >= conv_before && after <= 10.0 * before) continue;
         swi::launch_copy_block(c->U.as<double2>() + lo, n, Unew.as<double2>() + lo, n, c->N, ng, c->stream,
                                &c->launches);
         SWI_CUDA_TRY(cudaMemcpyAsync(epsnew.as<double2>() + lo, c->eps.as<double2>() + lo, sizeof(double2) * ng,
@@ -1051,6 +1056,15 @@ swi_status swi_create(swi_ctx** out, int nx, int ny, int nz, double h, int bc, i
   return SWI_OK;
 }
 
+// the packed (V, Gamma) planes of the TMA-staged complex64 stencil, once both are set
+static void refresh_vg(swi_ctx* c) {
+  if (!c->has_V || !c->has_G) return;
+  const size_t nxp = (size_t)(c->nx + (c->nx & 1));
+  c->VG32.ensure(sizeof(float2) * nxp * c->ny * c->nz);
+  swi::launch_pack_vg(c->V32.as<float>(), c->G32.as<float>(), c->nx, c->ny, c->nz, c->VG32.as<float2>(), c->stream);
+  sync(c->stream);
+}
+
 swi_status swi_set_potential(swi_ctx* c, const double* V, int on_device) {
   return guarded(c, [&]() -> swi_status {
     if (!V) return fail(c, SWI_EINVAL, "V is NULL");
@@ -1073,6 +1087,7 @@ swi_status swi_set_potential(swi_ctx* c, const double* V, int on_device) {
     sync(c->stream);
     c->maxabsV = mx;
     c->has_V = true;
+    refresh_vg(c);
     return SWI_OK;
   });
 }
@@ -1108,6 +1123,7 @@ swi_status swi_set_absorber(swi_ctx* c, const double* gL, const double* gR, int 
     c->maxG = mx;
     c->has_G = true;
     c->have_RL = false;
+    refresh_vg(c);
     return SWI_OK;
   });
 }
@@ -1211,6 +1227,7 @@ swi_status swi_apply_c64(swi_ctx* c, int nvec, const float* sigma, const void* X
     for (int m = 0; m < 7; ++m) P.cm[m] = (float)(-kFD[m] / (2.0 * c->h * c->h));
     P.V = c->V32.as<float>();
     P.G = c->G32.as<float>();
+    P.VG = c->VG32.as<float2>();
     const double Nn = (double)c->N;
     if (on_device) {
       ProfScope ps(c, SWI_K_STENCIL, kStencilFlops * Nn * nvec, (16.0 * nvec + 8.0) * Nn);
@@ -1508,6 +1525,43 @@ const char* swi_last_error(const swi_ctx* c) {
 }
 
 long long swi_launch_count(const swi_ctx* c) { return c ? c->launches : 0; }
+
+swi_status swi_check_schur(swi_ctx* c, int m, int b, int keep, const double* H, const double* B, int arith,
+                           double* T_out, double* Z_out, int* info_out) {
+  return guarded(c, [&]() -> swi_status {
+    if (m < 2 || m > 1024 || (b != 1 && b != 2) || keep < 1 || keep > m - b || !H || !T_out || !Z_out || !info_out)
+      return fail(c, SWI_EINVAL, "check_schur: bad arguments");
+    if (arith != SWI_ARITH_DS && arith != SWI_ARITH_F64) return fail(c, SWI_EINVAL, "unknown arithmetic");
+    const size_t mm = (size_t)m * m;
+    DevMem dH, dZ, dB, dBz, dth, dres, dS, dinfo, dHw, dZw;
+    dH.ensure(sizeof(double2) * mm);
+    dZ.ensure(sizeof(double2) * mm);
+    dS.ensure(sizeof(double2) * mm);
+    dB.ensure(sizeof(double2) * b * m);
+    dBz.ensure(sizeof(double2) * b * m);
+    dth.ensure(sizeof(double2) * m);
+    dres.ensure(sizeof(double) * m);
+    dinfo.ensure(sizeof(int) * 4);
+    dHw.ensure(16 * mm);
+    dZw.ensure(16 * mm);
+    SWI_CUDA_TRY(cudaMemcpyAsync(dH.p, H, sizeof(double2) * mm, cudaMemcpyHostToDevice, c->stream));
+    if (B) SWI_CUDA_TRY(cudaMemcpyAsync(dB.p, B, sizeof(double2) * b * m, cudaMemcpyHostToDevice, c->stream));
+    else SWI_CUDA_TRY(cudaMemsetAsync(dB.p, 0, sizeof(double2) * b * m, c->stream));
+    SWI_CUDA_TRY(cudaMemsetAsync(dinfo.p, 0, sizeof(int) * 4, c->stream));
+    swi::SchurBatch sb;
+    sb.n = 1;
+    sb.job[0] = swi::SchurJob{dH.as<double2>(), dZ.as<double2>(), dB.as<double2>(), dBz.as<double2>(),
+                              dth.as<double2>(), dres.as<double>(), dS.as<double2>(), dinfo.as<int>(),
+                              m, m, b, keep, keep, m - b, 0.0, dHw.p, dZw.p};
+    if (arith == SWI_ARITH_F64) swi::launch_schur_batch(sb, c->stream, &c->launches);
+    else swi::launch_schur_ds_batch(sb, c->stream, &c->launches);
+    SWI_CUDA_TRY(cudaMemcpyAsync(T_out, dH.p, sizeof(double2) * mm, cudaMemcpyDeviceToHost, c->stream));
+    SWI_CUDA_TRY(cudaMemcpyAsync(Z_out, dZ.p, sizeof(double2) * mm, cudaMemcpyDeviceToHost, c->stream));
+    SWI_CUDA_TRY(cudaMemcpyAsync(info_out, dinfo.p, sizeof(int) * 4, cudaMemcpyDeviceToHost, c->stream));
+    sync(c->stream);
+    return SWI_OK;
+  });
+}
 
 void swi_destroy(swi_ctx* c) {
   if (!c) return;

@@ -77,6 +77,7 @@ struct swi_ctx {
   int bc = SWI_BC_ODD, precision = SWI_PREC_F64;
   DevMem V, G, gL, gR;
   DevMem V32, G32;  // FP32 copies for the complex64 stencil
+  DevMem VG32;      // (V, Gamma) pairs with even row length, for the TMA-staged stencil
   bool has_V = false, has_G = false;
   double maxabsV = 0.0, maxG = 0.0;
   std::vector<double> sigma;

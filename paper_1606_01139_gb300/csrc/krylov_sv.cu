@@ -16,9 +16,10 @@
 //
 //  sv_gram_kernel:   part[chunk][i][b] = sum_{rows of chunk} conj(Q[r, i]) w[r, b]
 //                    (a block per 32-column slab and row chunk, one column per lane)
-//  sv_update_kernel: w[r, :] -= Q[r, :] c (a warp per row), then either the next
-//                    Gram's partials (FUSE_GRAM, the row's values reused from
-//                    registers: one read of Q for both passes) or w^H w
+//  sv_update_kernel: w[r, :] -= Q[r, :] c (a warp per row), then (FUSE_GRAM)
+//                    the next Gram's partials, the row's values reused from
+//                    registers: one read of Q for both passes
+//  sv_wgram_kernel:  part[chunk][a][b] = sum_{rows of chunk} conj(w[r, a]) w[r, b]
 //  sv_reduce_kernel: FP64 sums of the chunk partials, added into columns of H;
 //                    for w^H w the Cholesky factor of the block (Cholesky-QR)
 // Chunks hold at most 1024 rows: the per-lane FP32 (or double-single) partial
@@ -36,6 +37,19 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 
 // ----------------------------------------------------------------- arithmetic policies
+// w^H w entries are accumulated in double-single (heads and error terms of the
+// real and imaginary parts) by lane 0 of a warp, on the FP32 pipe
+struct Gds {
+  float rh, re, ih, ie;
+};
+__device__ __forceinline__ void gds_acc(Gds& a, float xrh, float xrl, float xih, float xil, float yrh, float yrl,
+                                        float yih, float yil) {  // a += conj(x) y
+  ds::fma_acc(a.rh, a.re, xrh, xrl, yrh, yrl);
+  ds::fma_acc(a.rh, a.re, xih, xil, yih, yil);
+  ds::fma_acc(a.ih, a.ie, xrh, xrl, yih, yil);
+  ds::fma_acc(a.ih, a.ie, -xih, -xil, yrh, yrl);
+}
+
 struct PolC64 {
   using T = float2;   // basis element
   using A = float2;   // accumulator
@@ -62,8 +76,24 @@ struct PolC64 {
     return make_float2(__shfl_xor_sync(0xffffffffu, a.x, o), __shfl_xor_sync(0xffffffffu, a.y, o));
   }
   __device__ static double2 to_d(A a) { return make_double2(a.x, a.y); }
-  __device__ static T sub(T w, A d) { return make_float2(w.x - d.x, w.y - d.y); }
   __device__ static T from_c(double2 c) { return make_float2((float)c.x, (float)c.y); }
+  // the new vectors w: complex64, like the basis
+  using W = float2;
+  __device__ static S wload(W v) { return v; }
+  __device__ static W wstore(S v) { return v; }
+  __device__ static S wsub(S w, A d) { return make_float2(w.x - d.x, w.y - d.y); }
+  __device__ static void gacc(Gds& g, S x, S y) { gds_acc(g, x.x, 0.f, x.y, 0.f, y.x, 0.f, y.y, 0.f); }
+  __device__ static double2 wto_d(W v) { return make_double2(v.x, v.y); }
+  __device__ static W wfrom_d(double2 v) { return make_float2((float)v.x, (float)v.y); }
+  // the FP32 passes: the same arithmetic
+  using F = float2;
+  __device__ static F fzero() { return make_float2(0.f, 0.f); }
+  __device__ static void fconj_mac(F& a, T q, S w) { conj_mac(a, q, w); }
+  __device__ static void fmac(F& a, T q, S c) { mac(a, q, c); }
+  __device__ static F fadd(F a, F b) { return add(a, b); }
+  __device__ static F fshfl_xor(F a, int o) { return shfl_xor(a, o); }
+  __device__ static double2 fto_d(F a) { return to_d(a); }
+  __device__ static A fto_A(F a) { return a; }
 };
 
 // x = hi + lo from the bit fields alone (integer and FP32 pipes only): hi is x
@@ -72,6 +102,16 @@ struct PolC64 {
 // entries, new vectors and coefficients of the loop lie far inside that range,
 // and no FP64 instruction is issued (a predicated FP64 fallback would occupy
 // GB300's narrow FP64 pipe on every element).
+__device__ __forceinline__ float hi_fast(double x) {  // the head of split_fast alone
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned int top = (unsigned int)(b >> 32);
+  const int e0 = (int)((top >> 20) & 0x7ff);
+  const int e = min(max(e0, 949), 1149);
+  const unsigned int fb =
+      ((unsigned int)(e - 896) << 23 | ((unsigned int)(b >> 29) & 0x7fffffu)) + ((unsigned int)(b >> 28) & 1u);
+  return e0 < 949 ? 0.f : __uint_as_float((top & 0x80000000u) | fb);
+}
+
 __device__ __forceinline__ void split_fast(double x, float& hi, float& lo) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const unsigned int top = (unsigned int)(b >> 32);
@@ -130,15 +170,50 @@ struct PolDs {
              __shfl_xor_sync(0xffffffffu, a.ih, o), __shfl_xor_sync(0xffffffffu, a.ie, o)};
   }
   __device__ static double2 to_d(A a) { return make_double2((double)a.rh + (double)a.re, (double)a.ih + (double)a.ie); }
-  __device__ static T sub(T w, A d) {
-    const double2 dd = to_d(d);
-    return make_double2(w.x - dd.x, w.y - dd.y);
-  }
   __device__ static T from_c(double2 c) { return c; }
+  // the new vectors w: kept in split form (heads and tails as floats) while
+  // they are orthogonalised, so that forming w - Q c takes no FP64 instruction
+  using W = float4;
+  __device__ static S wload(W v) { return S{v.x, v.y, v.z, v.w}; }
+  __device__ static W wstore(S v) { return make_float4(v.rh, v.rl, v.ih, v.il); }
+  __device__ static S wsub(S w, A d) {  // w - d, renormalised to head + tail
+    const ds::df r = ds::add(ds::df{w.rh, w.rl}, ds::df{-d.rh, -d.re});
+    const ds::df i = ds::add(ds::df{w.ih, w.il}, ds::df{-d.ih, -d.ie});
+    return S{r.h, r.l, i.h, i.l};
+  }
+  __device__ static void gacc(Gds& g, S x, S y) { gds_acc(g, x.rh, x.rl, x.ih, x.il, y.rh, y.rl, y.ih, y.il); }
+  __device__ static double2 wto_d(W v) { return make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w); }
+  __device__ static W wfrom_d(double2 v) {
+    S o;
+    split_fast(v.x, o.rh, o.rl);
+    split_fast(v.y, o.ih, o.il);
+    return wstore(o);
+  }
+  // the FP32 passes: products of the heads in FP32 (the first Gram of
+  // classical Gram-Schmidt twice, and the update by the second pass's small
+  // coefficients, need no more)
+  using F = float2;
+  __device__ static F fzero() { return make_float2(0.f, 0.f); }
+  __device__ static void fconj_mac(F& a, T q, const S& w) {  // a += conj(q) w
+    const float qr = hi_fast(q.x), qi = hi_fast(q.y);
+    a.x = fmaf(qr, w.rh, fmaf(qi, w.ih, a.x));
+    a.y = fmaf(qr, w.ih, fmaf(-qi, w.rh, a.y));
+  }
+  __device__ static void fmac(F& a, T q, const S& c) {  // a += q c
+    const float qr = hi_fast(q.x), qi = hi_fast(q.y);
+    a.x = fmaf(qr, c.rh, fmaf(-qi, c.ih, a.x));
+    a.y = fmaf(qr, c.ih, fmaf(qi, c.rh, a.y));
+  }
+  __device__ static F fadd(F a, F b) { return make_float2(a.x + b.x, a.y + b.y); }
+  __device__ static F fshfl_xor(F a, int o) {
+    return make_float2(__shfl_xor_sync(0xffffffffu, a.x, o), __shfl_xor_sync(0xffffffffu, a.y, o));
+  }
+  __device__ static double2 fto_d(F a) { return make_double2(a.x, a.y); }
+  __device__ static A fto_A(F a) { return A{a.x, 0.f, a.y, 0.f}; }
 };
 
 // ----------------------------------------------------------------- Gram pass
-template <class Pol, int NB>
+template <class Pol, int NB, bool FAST>
 __global__ void __launch_bounds__(kThreads) sv_gram_kernel(const __grid_constant__ SvBatch batch, int N, int rpc) {
   using T = typename Pol::T;
   using A = typename Pol::A;
@@ -146,33 +221,58 @@ __global__ void __launch_bounds__(kThreads) sv_gram_kernel(const __grid_constant
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int col = blockIdx.y * 32 + lane;
   if (blockIdx.y * 32 >= J.ncols) return;  // this job has fewer slabs (uniform over the block)
+  using Wt = typename Pol::W;
   const T* __restrict__ Q = static_cast<const T*>(J.Q);
-  const T* __restrict__ w = static_cast<const T*>(J.w);
+  const Wt* __restrict__ w = static_cast<const Wt*>(J.w);
   const int r0 = blockIdx.x * rpc, r1 = min(N, r0 + rpc);
   const bool on = col < J.ncols;
-  // two interleaved accumulators per lane and column of w (instruction-level parallelism)
-  A a0[NB], a1[NB];
-#pragma unroll
-  for (int b = 0; b < NB; ++b) a0[b] = a1[b] = Pol::zero();
-  int r = r0 + warp;
-  for (; r + kWarps < r1; r += 2 * kWarps) {
-    const T q0 = on ? __ldg(Q + (long long)r * J.ldq + col) : T{};
-    const T q1 = on ? __ldg(Q + (long long)(r + kWarps) * J.ldq + col) : T{};
-    const auto s0 = Pol::split(q0), s1 = Pol::split(q1);
-#pragma unroll
-    for (int b = 0; b < NB; ++b) {
-      Pol::conj_mac_s(a0[b], s0, Pol::split(w[(long long)r * J.ldw + b]));
-      Pol::conj_mac_s(a1[b], s1, Pol::split(w[(long long)(r + kWarps) * J.ldw + b]));
-    }
-  }
-  if (r < r1) {
-    const auto s0 = Pol::split(on ? __ldg(Q + (long long)r * J.ldq + col) : T{});
-#pragma unroll
-    for (int b = 0; b < NB; ++b) Pol::conj_mac_s(a0[b], s0, Pol::split(w[(long long)r * J.ldw + b]));
-  }
   __shared__ double2 red[kWarps][NB][32];
+  int r = r0 + warp;
+  if constexpr (FAST) {
+    // four rows per iteration, their loads issued together (memory-level
+    // parallelism), two interleaved accumulators per column of w
+    typename Pol::F a0[NB], a1[NB];
 #pragma unroll
-  for (int b = 0; b < NB; ++b) red[warp][b][lane] = Pol::to_d(Pol::add(a0[b], a1[b]));
+    for (int b = 0; b < NB; ++b) a0[b] = a1[b] = Pol::fzero();
+    for (; r + 3 * kWarps < r1; r += 4 * kWarps) {
+      T q[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) q[u] = on ? __ldg(Q + (long long)(r + u * kWarps) * J.ldq + col) : T{};
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+          Pol::fconj_mac((u & 1) ? a1[b] : a0[b], q[u], Pol::wload(w[(long long)(r + u * kWarps) * J.ldw + b]));
+    }
+    for (; r < r1; r += kWarps) {
+      const T q0 = on ? __ldg(Q + (long long)r * J.ldq + col) : T{};
+#pragma unroll
+      for (int b = 0; b < NB; ++b) Pol::fconj_mac(a0[b], q0, Pol::wload(w[(long long)r * J.ldw + b]));
+    }
+#pragma unroll
+    for (int b = 0; b < NB; ++b) red[warp][b][lane] = Pol::fto_d(Pol::fadd(a0[b], a1[b]));
+  } else {
+    A a0[NB], a1[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) a0[b] = a1[b] = Pol::zero();
+    for (; r + kWarps < r1; r += 2 * kWarps) {
+      const T q0 = on ? __ldg(Q + (long long)r * J.ldq + col) : T{};
+      const T q1 = on ? __ldg(Q + (long long)(r + kWarps) * J.ldq + col) : T{};
+      const auto s0 = Pol::split(q0), s1 = Pol::split(q1);
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        Pol::conj_mac_s(a0[b], s0, Pol::wload(w[(long long)r * J.ldw + b]));
+        Pol::conj_mac_s(a1[b], s1, Pol::wload(w[(long long)(r + kWarps) * J.ldw + b]));
+      }
+    }
+    if (r < r1) {
+      const auto s0 = Pol::split(on ? __ldg(Q + (long long)r * J.ldq + col) : T{});
+#pragma unroll
+      for (int b = 0; b < NB; ++b) Pol::conj_mac_s(a0[b], s0, Pol::wload(w[(long long)r * J.ldw + b]));
+    }
+#pragma unroll
+    for (int b = 0; b < NB; ++b) red[warp][b][lane] = Pol::to_d(Pol::add(a0[b], a1[b]));
+  }
   __syncthreads();
   if (warp == 0 && on) {
 #pragma unroll
@@ -192,7 +292,7 @@ __global__ void __launch_bounds__(kThreads) sv_gram_kernel(const __grid_constant
 // A warp per row; lane l holds basis columns l, l + 32, ... (NT of them, the
 // row's values kept in registers for the fused Gram).
 template <class Pol, int NT, int NB, bool FUSE_GRAM>
-__global__ void __launch_bounds__(kThreads) sv_update_kernel(const __grid_constant__ SvBatch batch, int N, int rpc) {
+__global__ void __launch_bounds__(kThreads, (NT <= 8 && (NB == 1 || !FUSE_GRAM)) ? 2 : 1) sv_update_kernel(const __grid_constant__ SvBatch batch, int N, int rpc) {
   using T = typename Pol::T;
   using A = typename Pol::A;
   using Sp = typename Pol::S;
@@ -206,8 +306,9 @@ __global__ void __launch_bounds__(kThreads) sv_update_kernel(const __grid_consta
   double2* red = sh + (size_t)ncols * NB;
   for (int i = threadIdx.x; i < ncols * NB; i += kThreads) cs[i] = Pol::split(Pol::from_c(J.c[i]));
   __syncthreads();
+  using Wt = typename Pol::W;
   const T* __restrict__ Q = static_cast<const T*>(J.Q);
-  T* w = static_cast<T*>(J.w);
+  Wt* w = static_cast<Wt*>(J.w);
   const int r0 = blockIdx.x * rpc, r1 = min(N, r0 + rpc);
   constexpr int NA = FUSE_GRAM ? NT : 1;
   A acc[NA][NB];
@@ -215,51 +316,62 @@ __global__ void __launch_bounds__(kThreads) sv_update_kernel(const __grid_consta
   for (int t = 0; t < NA; ++t)
 #pragma unroll
     for (int b = 0; b < NB; ++b) acc[t][b] = Pol::zero();
-  double2 g[NB * NB];  // lane 0: w^H w of its rows (FP64)
-#pragma unroll
-  for (int e = 0; e < NB * NB; ++e) g[e] = make_double2(0.0, 0.0);
   for (int r = r0 + warp; r < r1; r += kWarps) {
-    Sp q[NT];
-#pragma unroll
-    for (int t = 0; t < NT; ++t) {
-      const int i = lane + 32 * t;
-      q[t] = Pol::split(i < ncols ? __ldg(Q + (long long)r * J.ldq + i) : T{});
-    }
+    // the row's basis values (split once when the fused Gram reuses them)
+    Sp q[FUSE_GRAM ? NT : 1];
     A d[NB];
+    if constexpr (!FUSE_GRAM) {
+      // the update by the second pass's coefficients: products of the heads in FP32
+      T qr[NT];
 #pragma unroll
-    for (int b = 0; b < NB; ++b) d[b] = Pol::zero();
+      for (int t = 0; t < NT; ++t) {
+        const int i = lane + 32 * t;
+        qr[t] = i < ncols ? __ldg(Q + (long long)r * J.ldq + i) : T{};
+      }
+      typename Pol::F f[NB];
 #pragma unroll
-    for (int t = 0; t < NT; ++t) {
-      const int i = lane + 32 * t;
-      if (i < ncols)
+      for (int b = 0; b < NB; ++b) f[b] = Pol::fzero();
 #pragma unroll
-        for (int b = 0; b < NB; ++b) Pol::mac_s(d[b], q[t], cs[i * NB + b]);
-    }
+      for (int t = 0; t < NT; ++t) {
+        const int i = lane + 32 * t;
+        if (i < ncols)
 #pragma unroll
-    for (int b = 0; b < NB; ++b)
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) d[b] = Pol::add(d[b], Pol::shfl_xor(d[b], o));
-    // the row's new values are formed by lane 0 alone (in the complex128 form
-    // that takes FP64 instructions, kept off the other 31 lanes) and their
-    // split forms broadcast
-    Sp ws[NB]{};
-    if (lane == 0) {
-      T wv[NB];
+          for (int b = 0; b < NB; ++b) Pol::fmac(f[b], qr[t], cs[i * NB + b]);
+      }
 #pragma unroll
       for (int b = 0; b < NB; ++b) {
-        wv[b] = Pol::sub(w[(long long)r * J.ldw + b], d[b]);
-        w[(long long)r * J.ldw + b] = wv[b];
-        if (FUSE_GRAM) ws[b] = Pol::split(wv[b]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) f[b] = Pol::fadd(f[b], Pol::fshfl_xor(f[b], o));
+        d[b] = Pol::fto_A(f[b]);
       }
-      if (!FUSE_GRAM) {
+    } else {
 #pragma unroll
-        for (int a = 0; a < NB; ++a)
+      for (int t = 0; t < NT; ++t) {
+        const int i = lane + 32 * t;
+        q[t] = Pol::split(i < ncols ? __ldg(Q + (long long)r * J.ldq + i) : T{});
+      }
 #pragma unroll
-          for (int b = 0; b < NB; ++b) {
-            const double ar = wv[a].x, ai = wv[a].y, br = wv[b].x, bi = wv[b].y;
-            g[a * NB + b].x += ar * br + ai * bi;
-            g[a * NB + b].y += ar * bi - ai * br;
-          }
+      for (int b = 0; b < NB; ++b) d[b] = Pol::zero();
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        const int i = lane + 32 * t;
+        if (i < ncols)
+#pragma unroll
+          for (int b = 0; b < NB; ++b) Pol::mac_s(d[b], q[t], cs[i * NB + b]);
+      }
+#pragma unroll
+      for (int b = 0; b < NB; ++b)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) d[b] = Pol::add(d[b], Pol::shfl_xor(d[b], o));
+    }
+    // the row's new values are formed by lane 0 alone (FP32 instructions
+    // only, in split form) and broadcast
+    Sp ws[NB]{};
+    if (lane == 0) {
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        ws[b] = Pol::wsub(Pol::wload(w[(long long)r * J.ldw + b]), d[b]);
+        w[(long long)r * J.ldw + b] = Pol::wstore(ws[b]);
       }
     }
     if (FUSE_GRAM) {
@@ -268,25 +380,11 @@ __global__ void __launch_bounds__(kThreads) sv_update_kernel(const __grid_consta
 #pragma unroll
       for (int t = 0; t < NT; ++t)
 #pragma unroll
-        for (int b = 0; b < NB; ++b) Pol::conj_mac_s(acc[FUSE_GRAM ? t : 0][b], q[t], ws[b]);
+        for (int b = 0; b < NB; ++b) Pol::conj_mac_s(acc[FUSE_GRAM ? t : 0][b], q[FUSE_GRAM ? t : 0], ws[b]);
     }
   }
   double2* out = J.part + (long long)blockIdx.x * J.ldp;
-  if (!FUSE_GRAM) {
-    if (lane == 0)
-#pragma unroll
-      for (int e = 0; e < NB * NB; ++e) red[warp * NB * NB + e] = g[e];  // lane 0 holds its warp's rows
-    __syncthreads();
-    if (threadIdx.x < NB * NB) {
-      double2 s = make_double2(0.0, 0.0);
-      for (int k = 0; k < kWarps; ++k) {
-        s.x += red[k * NB * NB + threadIdx.x].x;
-        s.y += red[k * NB * NB + threadIdx.x].y;
-      }
-      out[threadIdx.x] = s;
-    }
-    return;
-  }
+  if (!FUSE_GRAM) return;
   // cross-warp sums, one 32-column slab at a time: red [kWarps][NB][32]
 #pragma unroll
   for (int t = 0; t < NT; ++t) {
@@ -307,6 +405,44 @@ __global__ void __launch_bounds__(kThreads) sv_update_kernel(const __grid_consta
     }
     __syncthreads();
   }
+}
+
+// ----------------------------------------------------------------- w^H w of the new block
+// A block per row chunk and job, a thread per row (strided): double-single
+// products on every lane, FP64 sums across the block.
+template <class Pol, int NB>
+__global__ void __launch_bounds__(kThreads) sv_wgram_kernel(const __grid_constant__ SvBatch batch, int N, int rpc) {
+  using Wt = typename Pol::W;
+  const SvJob& J = batch.job[blockIdx.y];
+  const Wt* __restrict__ w = static_cast<const Wt*>(J.w);
+  const int r0 = blockIdx.x * rpc, r1 = min(N, r0 + rpc);
+  Gds g[NB * NB];
+#pragma unroll
+  for (int e = 0; e < NB * NB; ++e) g[e] = Gds{0.f, 0.f, 0.f, 0.f};
+  for (int r = r0 + threadIdx.x; r < r1; r += kThreads) {
+    typename Pol::S v[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) v[b] = Pol::wload(w[(long long)r * J.ldw + b]);
+#pragma unroll
+    for (int a = 0; a < NB; ++a)
+#pragma unroll
+      for (int b = 0; b < NB; ++b) Pol::gacc(g[a * NB + b], v[a], v[b]);
+  }
+  __shared__ double2 red[NB * NB][kThreads];
+#pragma unroll
+  for (int e = 0; e < NB * NB; ++e)
+    red[e][threadIdx.x] = make_double2((double)g[e].rh + (double)g[e].re, (double)g[e].ih + (double)g[e].ie);
+  __syncthreads();
+  for (int st = kThreads / 2; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st)
+#pragma unroll
+      for (int e = 0; e < NB * NB; ++e) {
+        red[e][threadIdx.x].x += red[e][threadIdx.x + st].x;
+        red[e][threadIdx.x].y += red[e][threadIdx.x + st].y;
+      }
+    __syncthreads();
+  }
+  if (threadIdx.x < NB * NB) J.part[(long long)blockIdx.x * J.ldp + threadIdx.x] = red[threadIdx.x][0];
 }
 
 // ----------------------------------------------------------------- chunk reduction
@@ -417,23 +553,20 @@ __global__ void __launch_bounds__(32 * kRedLanes) sv_reduce_kernel(const __grid_
 }
 
 // ----------------------------------------------------------------- normalisation
-template <class T, int NB>
+template <class Pol, int NB>
 __global__ void sv_normalize_kernel(const __grid_constant__ SvNormBatch batch, int N) {
+  using T = typename Pol::T;
+  using Wt = typename Pol::W;
   const SvNormJob& J = batch.job[blockIdx.y];
   double2 r[NB * NB];
 #pragma unroll
   for (int e = 0; e < NB * NB; ++e) r[e] = J.r[e];
-  const T* w = static_cast<const T*>(J.w);
-  T* d1 = static_cast<T*>(J.dst1);
-  T* d2 = static_cast<T*>(J.dst2);
+  const Wt* w = static_cast<const Wt*>(J.w);
   for (long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x; row < N;
        row += (long long)gridDim.x * blockDim.x) {
     double2 v[NB];
 #pragma unroll
-    for (int a = 0; a < NB; ++a) {
-      const T x = w[row * J.ldw + a];
-      v[a] = make_double2((double)x.x, (double)x.y);
-    }
+    for (int a = 0; a < NB; ++a) v[a] = Pol::wto_d(w[row * J.ldw + a]);
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
       double re = 0.0, im = 0.0;
@@ -442,11 +575,15 @@ __global__ void sv_normalize_kernel(const __grid_constant__ SvNormBatch batch, i
         re += v[a].x * r[a * NB + b].x - v[a].y * r[a * NB + b].y;
         im += v[a].x * r[a * NB + b].y + v[a].y * r[a * NB + b].x;
       }
-      T o;
-      o.x = (decltype(o.x))re;
-      o.y = (decltype(o.y))im;
-      d1[row * J.ld1 + b] = o;
-      if (d2) d2[row * J.ld2 + b] = o;
+      if (J.out_w) {
+        static_cast<Wt*>(J.dst1)[row * J.ld1 + b] = Pol::wfrom_d(make_double2(re, im));
+      } else {
+        T o;
+        o.x = (decltype(o.x))re;
+        o.y = (decltype(o.y))im;
+        static_cast<T*>(J.dst1)[row * J.ld1 + b] = o;
+        if (J.dst2) static_cast<T*>(J.dst2)[row * J.ld2 + b] = o;
+      }
     }
   }
 }
@@ -477,11 +614,13 @@ void launch_pass_nb(const SvBatch& b, int mode, int N, int rpc, int maxcols, cud
   const int nchunks = (N + rpc - 1) / rpc;
   if (mode == SV_GRAM) {
     const dim3 grid(nchunks, (maxcols + 31) / 32, b.n);
-    sv_gram_kernel<Pol, NB><<<grid, kThreads, 0, s>>>(b, N, rpc);
+    sv_gram_kernel<Pol, NB, true><<<grid, kThreads, 0, s>>>(b, N, rpc);
   } else if (mode == SV_UPDATE_GRAM) {
     launch_update<Pol, NB, true>(b, N, rpc, maxcols, s);
-  } else {
+  } else if (mode == SV_UPDATE) {
     launch_update<Pol, NB, false>(b, N, rpc, maxcols, s);
+  } else {
+    sv_wgram_kernel<Pol, NB><<<dim3(nchunks, b.n), kThreads, 0, s>>>(b, N, rpc);
   }
 }
 
@@ -503,8 +642,8 @@ void launch_sv_pass(const SvBatch& b, int mode, bool ds, int nb, int N, int rpc,
   int maxcols = 0;
   for (int q = 0; q < b.n; ++q) {
     const int nc = b.job[q].ncols;
-    if (nc > 1024 || nc < 0 || (nc == 0 && mode != SV_UPDATE_NORM))
-      throw Error{SWI_EINVAL, "Gram-Schmidt pass: 1..1024 basis columns (0 only for w^H w)"};
+    if (nc > 1024 || (mode != SV_WGRAM && nc < 1))
+      throw Error{SWI_EINVAL, "Gram-Schmidt pass: 1..1024 basis columns"};
     maxcols = std::max(maxcols, nc);
   }
   if (rpc < 8 || rpc > 1024) throw Error{SWI_EINVAL, "Gram-Schmidt pass: rows per chunk out of range"};
@@ -540,11 +679,11 @@ void launch_sv_normalize(const SvNormBatch& b, bool ds, int nb, int N, cudaStrea
   const int blocks = std::min((N + 255) / 256, 1024);
   const dim3 grid(blocks, b.n);
   if (ds) {
-    if (nb == 1) sv_normalize_kernel<double2, 1><<<grid, 256, 0, s>>>(b, N);
-    else sv_normalize_kernel<double2, 2><<<grid, 256, 0, s>>>(b, N);
+    if (nb == 1) sv_normalize_kernel<PolDs, 1><<<grid, 256, 0, s>>>(b, N);
+    else sv_normalize_kernel<PolDs, 2><<<grid, 256, 0, s>>>(b, N);
   } else {
-    if (nb == 1) sv_normalize_kernel<float2, 1><<<grid, 256, 0, s>>>(b, N);
-    else sv_normalize_kernel<float2, 2><<<grid, 256, 0, s>>>(b, N);
+    if (nb == 1) sv_normalize_kernel<PolC64, 1><<<grid, 256, 0, s>>>(b, N);
+    else sv_normalize_kernel<PolC64, 2><<<grid, 256, 0, s>>>(b, N);
   }
   SWI_CHECK_LAUNCH();
   if (launches) ++*launches;

@@ -78,7 +78,9 @@ void launch_restart_h(double2* H, int ldh, int n, int kk, int nb, const double2*
   if (launches) ++*launches;
 }
 
-__global__ void random_col_c128_kernel(double2* __restrict__ dst, int ld, int rows, unsigned long long seed) {
+// a random start vector in the split form of the double-single loop (heads and
+// tails of the real and imaginary parts as floats)
+__global__ void random_col_ds_kernel(float4* __restrict__ dst, int ld, int rows, unsigned long long seed) {
   for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += (long long)gridDim.x * blockDim.x) {
     unsigned long long z = seed + 0x9E3779B97F4A7C15ull * (2 * r + 1);
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -88,8 +90,10 @@ __global__ void random_col_c128_kernel(double2* __restrict__ dst, int ld, int ro
     y = (y ^ (y >> 30)) * 0xBF58476D1CE4E5B9ull;
     y = (y ^ (y >> 27)) * 0x94D049BB133111EBull;
     y ^= y >> 31;
-    dst[r * ld] = make_double2((double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0,
-                               (double)(y >> 11) * (2.0 / 9007199254740992.0) - 1.0);
+    const double re = (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+    const double im = (double)(y >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+    const float rh = __double2float_rn(re), ih = __double2float_rn(im);
+    dst[r * ld] = make_float4(rh, __double2float_rn(re - rh), ih, __double2float_rn(im - ih));
   }
 }
 
@@ -102,6 +106,7 @@ swi::StencilC64Params stencil_c64_params(const swi_ctx* c) {
   for (int m = 0; m < 7; ++m) P.cm[m] = (float)(-kFD[m] / (2.0 * c->h * c->h));
   P.V = c->V32.as<float>();
   P.G = c->G32.as<float>();
+  P.VG = c->VG32.as<float2>();
   return P;
 }
 
@@ -136,9 +141,11 @@ swi_status solve_sv(swi_ctx* c, const swi_solve_opts& opt, swi_solve_info* info)
     w.nreq = c->nreq[j];
     w.col = j;
     int keep = opt.keep > 0 ? opt.keep : std::max(w.nreq + (w.nreq + 1) / 2, w.nreq + nb);
-    // the default basis leaves 128 to 144 steps per restart cycle (the stagger
-    // by window index keeps equal windows from restarting together)
-    int m = opt.max_basis > 0 ? opt.max_basis : std::max(2 * w.nreq + 1, keep + nb * (128 + 8 * (j % 3)));
+    // the default basis leaves room for 128 to 144 new vectors per restart
+    // cycle (the stagger by window index keeps equal windows from restarting
+    // together); it keeps the projected matrix near 230-250 for the usual
+    // requests, where its Schur step stays short
+    int m = opt.max_basis > 0 ? opt.max_basis : std::max(2 * w.nreq + 1, keep + 128 + 8 * (j % 3));
     if (keep > m - nb) keep = m - nb;
     if (keep < w.nreq) return fail(c, SWI_EINVAL, "max_basis too small for the window request");
     if (m > max_basis)
@@ -152,8 +159,9 @@ swi_status solve_sv(swi_ctx* c, const swi_solve_opts& opt, swi_solve_info* info)
     max_m = std::max(max_m, m);
     total_out += w.nreq;
   }
-  const int rpc = swi::sv_rows_per_chunk(c->N, nwin);
-  const int nchunks = (c->N + rpc - 1) / rpc;
+  // row chunks of the Gram-Schmidt passes: sized each step for the windows
+  // still expanding (at least 256 rows per chunk, so at most this many chunks)
+  const int max_chunks = (c->N + 255) / 256;
   for (int j = 0; j < nwin; ++j) {
     Win& w = *win[j];
     const size_t hh = (size_t)w.ldh * w.ldh;
@@ -173,7 +181,7 @@ swi_status solve_sv(swi_ctx* c, const swi_solve_opts& opt, swi_solve_info* info)
     w.C2.ensure(sizeof(double2) * w.ldh * nb);
     if (!DS) w.Z32.ensure(sizeof(float2) * hh);
     w.rinv.ensure(sizeof(double2) * 16);  // R^-1, R, breakdown flag
-    w.part.ensure(sizeof(double2) * (size_t)nchunks * w.ldh * nb);
+    w.part.ensure(sizeof(double2) * (size_t)max_chunks * w.ldh * nb);
     SWI_CUDA_TRY(cudaMemsetAsync(w.H.p, 0, sizeof(double2) * hh, c->stream));
     SWI_CUDA_TRY(cudaMemsetAsync(w.Q.p, 0, sizeof(T) * N * w.ldq, c->stream));
     SWI_CUDA_TRY(cudaMemsetAsync(w.rinv.p, 0, sizeof(double2) * 16, c->stream));
@@ -182,8 +190,9 @@ swi_status solve_sv(swi_ctx* c, const swi_solve_opts& opt, swi_solve_info* info)
   c->Uall.ensure(sizeof(double2) * N * n_all);
   c->ordinfo.ensure(sizeof(int) * 4 * nwin);
   // newest block of every window (columns [j nb, j nb + nb)) and its image
-  // under A - sigma_j; a complex128 work block for the restart rotations and
-  // the delivered Ritz vectors
+  // under A - sigma_j (in the double-single form the image is kept split, four
+  // floats per entry, while it is orthogonalised); a complex128 work block for
+  // the restart rotations and the delivered Ritz vectors
   DevMem Vcur, Wblk, sigt, Tmp;
   const int ncv = nwin * nb;
   const int ldv = ncv + (ncv & 1);  // even: 16-byte rows for the tensor-map-staged stencil
@@ -209,20 +218,20 @@ swi_status solve_sv(swi_ctx* c, const swi_solve_opts& opt, swi_solve_info* info)
       for (int c0 = 0; c0 < ncv; c0 += 32)
         sb.blk[sb.n++] = swi::StencilBlock{reinterpret_cast<const double2*>(Vcur.p) + c0,
                                            reinterpret_cast<double2*>(Wblk.p) + c0, ldv, ldv,
-                                           std::min(32, ncv - c0), c0};
+                                           std::min(32, ncv - c0), c0, 1};
       swi::launch_stencil_ds(P64, sb, sigt.as<double>(), c->stream, &c->launches);
     } else {
       swi::launch_stencil_c64(P32, Vcur.as<float2>(), ldv, Wblk.as<float2>(), ldv, ncv, sigt.as<float>(),
                               c->stream, &c->launches);
     }
   };
-  // Orthonormalise the blocks W[:, j nb : j nb + nb] of the given windows
-  // after their last Gram-Schmidt pass has left w^H w in the chunk partials
-  // (part): one Cholesky factor for nb = 1, Cholesky-QR twice for nb = 2; R
+  // Orthonormalise the blocks W[:, j nb : j nb + nb] of the given windows:
+  // w^H w, one Cholesky factor for nb = 1, Cholesky-QR twice for nb = 2; R
   // goes below the block's column of H (when hrow is set), the block into the
   // basis at column dst_col and into Vcur.
-  auto orthonormalise = [&](const std::vector<Win*>& ws, const std::vector<int>& dst_col, bool hrow) {
+  auto orthonormalise = [&](const std::vector<Win*>& ws, const std::vector<int>& dst_col, bool hrow, int rpc) {
     const int na = (int)ws.size();
+    const int nchunks = (c->N + rpc - 1) / rpc;
     swi::SvReduceBatch r1, r2;
     swi::SvNormBatch n1, n2;
     swi::SvBatch g;
@@ -238,24 +247,23 @@ swi_status solve_sv(swi_ctx* c, const swi_solve_opts& opt, swi_solve_info* info)
       g.job[q] = swi::SvJob{w.Q.p, w.ldq, 0, wc, ldv, nullptr, pp, w.ldh * nb};
       r2.job[q] = swi::SvReduceJob{pp, w.ldh * nb, nchunks, 0, nb, 2, nullptr, Hr, w.ldh, ri};
       if (nb == 1) {
-        n1.job[q] = swi::SvNormJob{wc, ldv, Qd, w.ldq, Vcur.as<T>() + w.col * nb, ldv, ri};
+        n1.job[q] = swi::SvNormJob{wc, ldv, Qd, w.ldq, Vcur.as<T>() + w.col * nb, ldv, ri, 0};
       } else {
-        n1.job[q] = swi::SvNormJob{wc, ldv, wc, ldv, nullptr, 0, ri};
-        n2.job[q] = swi::SvNormJob{wc, ldv, Qd, w.ldq, Vcur.as<T>() + w.col * nb, ldv, ri};
+        n1.job[q] = swi::SvNormJob{wc, ldv, wc, ldv, nullptr, 0, ri, 1};
+        n2.job[q] = swi::SvNormJob{wc, ldv, Qd, w.ldq, Vcur.as<T>() + w.col * nb, ldv, ri, 0};
       }
     }
+    swi::launch_sv_pass(g, swi::SV_WGRAM, DS, nb, c->N, rpc, c->stream, &c->launches);
     swi::launch_sv_reduce(r1, c->stream, &c->launches);
     swi::launch_sv_normalize(n1, DS, nb, c->N, c->stream, &c->launches);
     if (nb == 1) return;
-    swi::launch_sv_pass(g, swi::SV_UPDATE_NORM, DS, nb, c->N, rpc, c->stream, &c->launches);
+    swi::launch_sv_pass(g, swi::SV_WGRAM, DS, nb, c->N, rpc, c->stream, &c->launches);
     swi::launch_sv_reduce(r2, c->stream, &c->launches);
     swi::launch_sv_normalize(n2, DS, nb, c->N, c->stream, &c->launches);
   };
 
   // start blocks: random, orthonormalised, in columns [0, nb) of each basis and in Vcur
   {
-    swi::SvBatch gb;
-    gb.n = nwin;
     std::vector<Win*> all;
     std::vector<int> zero(nwin, 0);
     for (int j = 0; j < nwin; ++j) {
@@ -264,17 +272,14 @@ swi_status solve_sv(swi_ctx* c, const swi_solve_opts& opt, swi_solve_info* info)
       for (int b = 0; b < nb; ++b) {
         const unsigned long long sd = seed * 1000003ull + (unsigned long long)j * nb + b;
         if constexpr (DS)
-          random_col_c128_kernel<<<std::min((c->N + 255) / 256, 1024), 256, 0, c->stream>>>(
-              Wblk.as<double2>() + j * nb + b, ldv, c->N, sd);
+          random_col_ds_kernel<<<std::min((c->N + 255) / 256, 1024), 256, 0, c->stream>>>(
+              Wblk.as<float4>() + j * nb + b, ldv, c->N, sd);
         else
           swi::launch_random_col_c64(Wblk.as<float2>() + j * nb + b, ldv, c->N, sd, c->stream, &c->launches);
         SWI_CHECK_LAUNCH();
       }
-      gb.job[j] = swi::SvJob{w.Q.p, w.ldq, 0, Wblk.as<T>() + j * nb, ldv, nullptr, w.part.template as<double2>(),
-                             w.ldh * nb};
     }
-    swi::launch_sv_pass(gb, swi::SV_UPDATE_NORM, DS, nb, c->N, rpc, c->stream, &c->launches);
-    orthonormalise(all, zero, false);
+    orthonormalise(all, zero, false, swi::sv_rows_per_chunk(c->N, nwin));
   }
 
   const double tol_abs = rel_tol * anorm;
@@ -419,14 +424,16 @@ swi_status solve_sv(swi_ctx* c, const swi_solve_opts& opt, swi_solve_info* info)
     }
     const int na = (int)act.size();
     const double Nn = (double)c->N;
+    const int rpc = swi::sv_rows_per_chunk(c->N, na);
+    const int nchunks = (c->N + rpc - 1) / rpc;
     // 1) W[:, j nb : j nb + nb] = (A - sigma_j) Q_j[:, p : p + nb] for every window
     //    (columns of waiting windows are computed and ignored)
     {
       ProfScope ps(c, SWI_K_STENCIL, kStencilFlops * Nn * ncv, (2.0 * sizeof(T) * ncv + 8.0) * Nn);
       apply_all();
     }
-    // 2) classical Gram-Schmidt twice against Q[:, 0:p+nb], then w^H w:
-    //    Gram, update fused with the second Gram, update fused with w^H w
+    // 2) classical Gram-Schmidt twice against Q[:, 0:p+nb]: Gram, update
+    //    fused with the second Gram, update; then the block's Cholesky-QR
     double ncol = 0.0;
     swi::SvBatch g0, g1, g2;
     swi::SvReduceBatch r0, r1;
@@ -459,8 +466,8 @@ swi_status solve_sv(swi_ctx* c, const swi_solve_opts& opt, swi_solve_info* info)
     }
     {
       ProfScope ps(c, SWI_K_UPDATE, 8.0 * Nn * ncol * nb, sizeof(T) * Nn * ncol + 2.0 * sizeof(T) * Nn * na * nb);
-      swi::launch_sv_pass(g2, swi::SV_UPDATE_NORM, DS, nb, c->N, rpc, c->stream, &c->launches);
-      orthonormalise(act, dst, true);
+      swi::launch_sv_pass(g2, swi::SV_UPDATE, DS, nb, c->N, rpc, c->stream, &c->launches);
+      orthonormalise(act, dst, true, rpc);
     }
     // 3) windows whose next block would not fit: projected eigenproblem on their own stream
     for (int q = 0; q < na; ++q) {

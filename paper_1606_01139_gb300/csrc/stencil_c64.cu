@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(kThreadsC64, 1)
 void launch_stencil_c64(const StencilC64Params& P, const float2* X, int ldx, float2* Y, int ldy, int ncols,
                         const float* sigma_dev, cudaStream_t s, long long* launches) {
   if (ncols <= 0) return;
-  if (stencil_c64_tma_ok(X, ldx)) {  // TMA-staged form (stencil_c64_tma.cu) for 16-byte aligned rows
+  if (P.VG != nullptr && stencil_c64_tma_ok(X, ldx)) {  // TMA-staged form (stencil_c64_tma.cu) for 16-byte aligned rows
     launch_stencil_c64_tma(P, X, ldx, Y, ldy, ncols, sigma_dev, s, launches);
     return;
   }

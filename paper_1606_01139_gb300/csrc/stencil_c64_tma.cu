@@ -2,22 +2,29 @@
 // matrix-free, shifted as in Eq. 3), staged by the tensor memory accelerator.
 //
 // The kernel is HBM-bound (16 bytes of vectors per output against ~40 packed
-// FP32 instructions), so it is organised for traffic:
+// FP32 instructions), so it is organised for traffic and latency:
 //  - a block owns a 32 x 8 tile of (x, y) points and a group of 4 columns
 //    (32 bytes, one sector per point) and marches along z;
 //  - the 4 column groups of a tile are adjacent in the grid, so they run
 //    together and read every 128-byte row of a 16-column block once from DRAM;
-//  - plane z of the tile with its 6-point halo (a 44 x 20 x 4 box) arrives in
-//    shared memory by one cp.async.bulk.tensor load, three planes in flight in
-//    a ring of stages, each completed on an mbarrier;
-//  - each thread computes two points stacked in y for one column: the
-//    y-neighbours of the pair come from one 14-value strip (19 shared loads
-//    per output instead of 24), the 12 z-neighbours from a register queue
-//    filled by loads two planes ahead (512 threads, 16 warps per SM);
-//  - the arithmetic is packed FP32x2 (re, im together).
+//  - plane j of the tile with its 6-point halo (a 44 x 20 x 4 box), and the
+//    plane's (V, Gamma) pairs of the tile, arrive in shared memory by
+//    cp.async.bulk.tensor loads, three planes in flight in a ring of four
+//    stages, each completed on an mbarrier; nothing else is read from global
+//    memory inside the loop;
+//  - the z direction is a forward sweep: when plane j lands, its value at a
+//    point is added (times the stencil weight) into the 13 pending outputs
+//    j - 6 .. j + 6 of that point, kept in a register ring; plane j's own
+//    output receives its x and y terms and the diagonal, and output j - 6 is
+//    then complete and stored.  The sweep runs over planes z0 - 6 .. z1 + 5
+//    of the block's z range (ghost planes by reflection or zero);
+//  - each thread computes two points stacked in y for one column (the y
+//    neighbours of the pair come from one 14-value strip); the arithmetic is
+//    packed FP32x2 (re, im together).
 // Ghost points: the tensor map fills out-of-range coordinates with zeros (the
 // zero rule, and the planes -1 and n of the odd rule); odd-reflection ghosts
-// further out are written into the staged box from their mirror points.
+// further out are written into the staged box from their mirror points, and
+// reflected z planes are loaded from their mirror plane with a sign.
 // Every mbarrier wait is bounded: on timeout the block records an error flag,
 // drains its copies in flight (again bounded) and returns.
 #include <cuda.h>
@@ -33,10 +40,13 @@ namespace {
 
 constexpr int kTX = 32, kTY = 8, kR = 6, kNC = 4;
 constexpr int kBX = kTX + 2 * kR, kBY = kTY + 2 * kR;  // staged box (44 x 20 points)
-constexpr int kStages = 3;
+constexpr int kStages = 4;
 constexpr int kThreads = kTX * (kTY / 2) * kNC;  // 512: two points (y, y + 1) per thread
-constexpr int kStageFloats = kBY * kBX * kNC * 2;       // 7040 floats = 28,160 bytes
+constexpr int kBoxFloats = kBY * kBX * kNC * 2;    // 7040 floats = 28,160 bytes
+constexpr int kVGFloats = kTY * kTX * 2;           // (V, Gamma) of the tile: 2,048 bytes
+constexpr int kStageFloats = kBoxFloats + kVGFloats;  // 30,208 bytes (a multiple of 128)
 constexpr unsigned kStageBytes = kStageFloats * 4;
+constexpr int kQ = 2 * kR + 1;  // pending outputs per point
 constexpr long long kSpinLimit = 1LL << 26;  // ~ seconds of polling: a lost copy, not a slow one
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -75,6 +85,15 @@ __device__ __forceinline__ void tma_load_4d(float* dst, const CUtensorMap* map, 
       : "memory");
 }
 
+__device__ __forceinline__ void tma_load_3d(float* dst, const CUtensorMap* map, unsigned long long* bar, int c0, int c1,
+                                            int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+      : "memory");
+}
+
 // source index and sign of axis index j on a line of n points (odd reflection
 // about the planes -1 and n, or zero); false for a zero ghost
 template <int BC>
@@ -93,16 +112,6 @@ __device__ __forceinline__ bool ghost_src(int j, int n, int& src, float& sgn) {
   return true;
 }
 
-template <int BC>
-__device__ __forceinline__ float2 load_z(const float2* __restrict__ X, long long pt_col, long long plane_ld, int z,
-                                         int nz, bool ok) {
-  int src;
-  float sgn;
-  if (!ok || !ghost_src<BC>(z, nz, src, sgn)) return make_float2(0.f, 0.f);
-  const float2 v = __ldg(X + pt_col + (long long)src * plane_ld);
-  return make_float2(sgn * v.x, sgn * v.y);
-}
-
 __device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
 
 }  // namespace
@@ -114,8 +123,8 @@ namespace {
 
 template <int BC>
 __global__ void __launch_bounds__(kThreads, 1)
-    stencil_c64_tma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ StencilC64Params P,
-                           const float2* __restrict__ X, int ldx, float2* __restrict__ Y, int ldy, int ncols,
+    stencil_c64_tma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap vgmap,
+                           const __grid_constant__ StencilC64Params P, float2* __restrict__ Y, int ldy, int ncols,
                            const float* __restrict__ sigma, int zchunk, int cgroups, int tiles_x) {
   extern __shared__ __align__(128) float stage_mem[];
   __shared__ __align__(8) unsigned long long bar[kStages];
@@ -132,17 +141,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int z0 = blockIdx.y * zchunk, z1 = min(P.nz, z0 + zchunk);
   const int xa = x0 + px, ya = y0 + 2 * py;  // the pair's first point
   const long long plane = (long long)P.nx * P.ny;
-  const long long plane_ld = plane * ldx;
   const bool colok = c < ncols;
-  bool ok[2][1];
-  long long ptc[2][1];
+  bool ok[2];
+  long long pto[2];  // (point index within a plane) * ldy + c
 #pragma unroll
-  for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-    for (int dx = 0; dx < 1; ++dx) {
-      ok[dy][dx] = colok && xa + dx < P.nx && ya + dy < P.ny;  // dx = 0: one point per row
-      ptc[dy][dx] = ((long long)(ya + dy) * P.nx + (xa + dx)) * ldx + c;
-    }
+  for (int dy = 0; dy < 2; ++dy) {
+    ok[dy] = colok && xa < P.nx && ya + dy < P.ny;
+    pto[dy] = ((long long)(ya + dy) * P.nx + xa) * ldy + c;
+  }
   float cm[kR + 1];
 #pragma unroll
   for (int m = 0; m <= kR; ++m) cm[m] = P.cm[m];
@@ -156,7 +162,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   __syncthreads();
   // odd-reflection ghosts inside the staged box (the same cells every plane):
-  // a list of (cell, mirror cell, sign) built once per block
+  // a list of (cell, mirror cell) built once per block
   const bool fixup = BC == SWI_BC_ODD && (x0 < kR || y0 < kR || x0 + kTX + kR > P.nx || y0 + kTY + kR > P.ny);
   if (fixup) {
     for (int e = tid; e < kBY * kBX; e += kThreads) {
@@ -177,122 +183,115 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
   }
   const int nghost = fixup ? s_nghost : 0;
-  // prologue: planes z0, z0 + 1 in flight
-  auto issue = [&](int z) {
-    const int s = (z - z0) % kStages;
+  // the sweep: source planes j = z0 - 6 + t, t < ns
+  const int js = z0 - kR, ns = (z1 - z0) + 2 * kR;
+  // plane j is loaded from plane zsrc(j) with sign sgn(j) (zsrc = -1: a zero plane)
+  auto src_plane = [&](int j, float& sgn) -> int {
+    int zs;
+    if (!ghost_src<BC>(j, P.nz, zs, sgn)) {
+      sgn = 0.f;
+      return -1;
+    }
+    return zs;
+  };
+  auto issue = [&](int t) {
+    const int s = t % kStages;
+    const int j = js + t;
+    float sg;
+    const int zsrc = src_plane(j, sg);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     mbar_expect_tx(&bar[s], kStageBytes);
-    tma_load_4d(stage_mem + s * kStageFloats, &tmap, &bar[s], 2 * c0, x0 - kR, y0 - kR, z);
+    float* st = stage_mem + s * kStageFloats;
+    tma_load_4d(st, &tmap, &bar[s], 2 * c0, x0 - kR, y0 - kR, zsrc);
+    tma_load_3d(st + kBoxFloats, &vgmap, &bar[s], 2 * x0, y0, (j >= z0 && j < z1) ? j : -1);
   };
   if (tid == 0) {
-    for (int z = z0; z < min(z1, z0 + kStages - 1); ++z) issue(z);
+    for (int t = 0; t < min(ns, kStages - 1); ++t) issue(t);
   }
 
-  // z queues of the two points, a ring of 13 planes: plane z0 - 6 + k in slot k
-  // (mod 13); the z loop is unrolled by 13 so every slot index is a constant
-  float2 q[2][1][2 * kR + 1];
+  float2 acc[2][kQ];  // pending outputs: plane js + t' in slot t' mod 13
 #pragma unroll
   for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
-    for (int dx = 0; dx < 1; ++dx)
-#pragma unroll
-      for (int k = 0; k < 2 * kR + 1; ++k) q[dy][dx][k] = load_z<BC>(X, ptc[dy][dx], plane_ld, z0 - kR + k, P.nz, ok[dy][dx]);
-
-  float vnext[2][1], gnext[2][1];
-  float2 nq1[2][1];
-#pragma unroll
-  for (int dy = 0; dy < 2; ++dy) nq1[dy][0] = load_z<BC>(X, ptc[dy][0], plane_ld, z0 + kR + 1, P.nz, ok[dy][0]);
-#pragma unroll
-  for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-    for (int dx = 0; dx < 1; ++dx) {
-      const long long pi = (long long)z0 * plane + (long long)(ya + dy) * P.nx + (xa + dx);
-      vnext[dy][dx] = ok[dy][dx] ? __ldg(P.V + pi) : 0.f;
-      gnext[dy][dx] = ok[dy][dx] ? __ldg(P.G + pi) : 0.f;
-    }
+    for (int k = 0; k < kQ; ++k) acc[dy][k] = make_float2(0.f, 0.f);
 
   bool bad = false;
-  int zs = z0;
-  for (int zb = z0; zb < z1 && !bad; zb += 2 * kR + 1) {
+  int tlast = 0;
+  for (int tb = 0; tb < ns && !bad; tb += kQ) {
 #pragma unroll
-    for (int j = 0; j < 2 * kR + 1; ++j) {
-      zs = zb + j;
-      if (zs >= z1) break;
-      const int s = (zs - z0) % kStages;
-      const unsigned parity = (unsigned)(((zs - z0) / kStages) & 1);
-      // queue entries two planes ahead and the local potential one plane ahead,
-      // loaded before the wait
-      float vv[2][1], gg[2][1];
-      float2 nq[2][1];
-#pragma unroll
-      for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-        for (int dx = 0; dx < 1; ++dx) {
-          nq[dy][dx] = nq1[dy][dx];
-          nq1[dy][dx] = load_z<BC>(X, ptc[dy][dx], plane_ld, zs + kR + 2, P.nz, ok[dy][dx]);
-          vv[dy][dx] = vnext[dy][dx];
-          gg[dy][dx] = gnext[dy][dx];
-          const long long pi = (long long)(zs + 1) * plane + (long long)(ya + dy) * P.nx + (xa + dx);
-          const bool ld = ok[dy][dx] && zs + 1 < z1;
-          vnext[dy][dx] = ld ? __ldg(P.V + pi) : 0.f;
-          gnext[dy][dx] = ld ? __ldg(P.G + pi) : 0.f;
-        }
-      if (tid == 0 && zs + kStages - 1 < z1) issue(zs + kStages - 1);
+    for (int u = 0; u < kQ; ++u) {
+      const int t = tb + u;
+      if (t >= ns) break;
+      tlast = t;
+      const int j = js + t;
+      const int s = t % kStages;
+      const unsigned parity = (unsigned)((t / kStages) & 1);
+      if (tid == 0 && t + kStages - 1 < ns) issue(t + kStages - 1);
       const bool landed = mbar_wait(&bar[s], parity);
       if (__syncthreads_or(!landed)) {  // one decision for the whole block
         bad = true;
         break;
       }
       float2* S2 = reinterpret_cast<float2*>(stage_mem + s * kStageFloats);  // [kBY][kBX][kNC]
-      if (nghost > 0) {  // -(mirror point) into every ghost cell of the box, all columns
+      const float2* VG = reinterpret_cast<const float2*>(stage_mem + s * kStageFloats + kBoxFloats);  // [kTY][kTX]
+      const bool real = j >= z0 && j < z1;  // an output plane of this block (uniform)
+      if (real && nghost > 0) {  // -(mirror point) into every ghost cell of the box, all columns
         for (int e = tid; e < nghost * kNC; e += kThreads) {
           const unsigned gcell = s_ghost[e / kNC];
           const int col = e % kNC;
-          const float2 u = S2[(gcell >> 16) * kNC + col];
-          S2[(gcell & 0xffffu) * kNC + col] = make_float2(-u.x, -u.y);
+          const float2 v = S2[(gcell >> 16) * kNC + col];
+          S2[(gcell & 0xffffu) * kNC + col] = make_float2(-v.x, -v.y);
         }
         __syncthreads();
       }
-      constexpr int Q = 2 * kR + 1;
-      float2 acc[2][1];
-#pragma unroll
-      for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-        for (int dx = 0; dx < 1; ++dx) {
-          const float2 u = q[dy][dx][(kR + j) % Q];
-          const float d = dcen + vv[dy][dx], gm = gg[dy][dx];
-          acc[dy][dx] = make_float2(fmaf(d, u.x, gm * u.y), fmaf(d, u.y, -gm * u.x));
-        }
-      // x neighbours of each point (13 values of its row)
-#pragma unroll
-      for (int dy = 0; dy < 2; ++dy) {
-        const float2* row = S2 + ((2 * py + dy + kR) * kBX + px) * kNC + cc;
-#pragma unroll
-        for (int m = 1; m <= kR; ++m)
-          acc[dy][0] = __ffma2_rn(make_float2(cm[m], cm[m]), f2add(row[(kR - m) * kNC], row[(kR + m) * kNC]), acc[dy][0]);
-      }
-      // y strip of the pair (14 values), together with the z queues
+      float sg;
+      src_plane(j, sg);
+      // the y strip of the pair (14 values); its entries 6 and 7 are the pair's own values
+      float2 sy[2 * kR + 2];
       {
-        float2 sy[2 * kR + 2];
         const float2* colp = S2 + ((2 * py) * kBX + px + kR) * kNC + cc;
 #pragma unroll
         for (int k = 0; k < 2 * kR + 2; ++k) sy[k] = colp[k * kBX * kNC];
-#pragma unroll
-        for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-          for (int m = 1; m <= kR; ++m) {
-            const float2 t = f2add(f2add(sy[dy + kR - m], sy[dy + kR + m]),
-                                   f2add(q[dy][0][(kR - m + j) % Q], q[dy][0][(kR + m + j) % Q]));
-            acc[dy][0] = __ffma2_rn(make_float2(cm[m], cm[m]), t, acc[dy][0]);
-          }
       }
 #pragma unroll
-      for (int dy = 0; dy < 2; ++dy)
+      for (int dy = 0; dy < 2; ++dy) {
+        const float2 uc = make_float2(sg * sy[dy + kR].x, sg * sy[dy + kR].y);
+        // z terms: plane j into the pending outputs j - 6 .. j + 6 (not j itself)
 #pragma unroll
-        for (int dx = 0; dx < 1; ++dx) {
-          if (ok[dy][dx]) Y[((long long)zs * plane + (long long)(ya + dy) * P.nx + (xa + dx)) * ldy + c] = acc[dy][dx];
-          q[dy][dx][j % Q] = nq[dy][dx];  // plane zs + 7 replaces plane zs - 6
+        for (int m = 1; m <= kR; ++m) {
+          const float2 w = make_float2(cm[m], cm[m]);
+          acc[dy][(u + kQ - m) % kQ] = __ffma2_rn(w, uc, acc[dy][(u + kQ - m) % kQ]);
+          acc[dy][(u + m) % kQ] = __ffma2_rn(w, uc, acc[dy][(u + m) % kQ]);
         }
+      }
+      if (real) {
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+          const float2 uc = sy[dy + kR];
+          const float2 vg = VG[(2 * py + dy) * kTX + px];
+          const float d = dcen + vg.x, gm = vg.y;
+          float2 a = acc[dy][u % kQ];
+          a.x += fmaf(d, uc.x, gm * uc.y);
+          a.y += fmaf(d, uc.y, -gm * uc.x);
+          // x neighbours (13 values of the point's row) and y neighbours (the strip)
+          const float2* row = S2 + ((2 * py + dy + kR) * kBX + px) * kNC + cc;
+#pragma unroll
+          for (int m = 1; m <= kR; ++m) {
+            const float2 t2 = f2add(f2add(row[(kR - m) * kNC], row[(kR + m) * kNC]),
+                                    f2add(sy[dy + kR - m], sy[dy + kR + m]));
+            a = __ffma2_rn(make_float2(cm[m], cm[m]), t2, a);
+          }
+          acc[dy][u % kQ] = a;
+        }
+      }
+      // output j - 6 is complete
+      const int o = j - kR;
+#pragma unroll
+      for (int dy = 0; dy < 2; ++dy) {
+        const int so = (u + kQ - kR) % kQ;
+        if (o >= z0 && ok[dy]) Y[(long long)o * plane * ldy + pto[dy]] = acc[dy][so];
+        acc[dy][so] = make_float2(0.f, 0.f);
+      }
       __syncthreads();  // stage s is free for the copy issued next step
     }
   }
@@ -300,10 +299,21 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (tid == 0) {
       atomicExch(&g_stencil_tma_err, 1);
       // drain the copies still in flight into this block's shared memory (bounded)
-      for (int z = zs; z < min(z1, zs + kStages); ++z)
-        mbar_wait(&bar[(z - z0) % kStages], (unsigned)(((z - z0) / kStages) & 1));
+      for (int t = tlast; t < min(ns, tlast + kStages); ++t)
+        mbar_wait(&bar[t % kStages], (unsigned)((t / kStages) & 1));
     }
     __syncthreads();
+  }
+}
+
+__global__ void pack_vg_kernel(const float* __restrict__ V, const float* __restrict__ G, int nx, int ny, int nz,
+                               int nxp, float2* __restrict__ VG) {
+  const long long total = (long long)nxp * ny * nz;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(e % nxp);
+    const long long row = e / nxp;  // z * ny + y
+    VG[e] = x < nx ? make_float2(V[row * nx + x], G[row * nx + x]) : make_float2(0.f, 0.f);
   }
 }
 
@@ -343,38 +353,61 @@ int stencil_c64_tma_error(bool clear) {
   return v;
 }
 
+void launch_pack_vg(const float* V, const float* G, int nx, int ny, int nz, float2* VG, cudaStream_t s) {
+  const int nxp = nx + (nx & 1);
+  const long long total = (long long)nxp * ny * nz;
+  pack_vg_kernel<<<(unsigned)std::min<long long>((total + 255) / 256, 4096), 256, 0, s>>>(V, G, nx, ny, nz, nxp, VG);
+  SWI_CHECK_LAUNCH();
+}
+
 void launch_stencil_c64_tma(const StencilC64Params& P, const float2* X, int ldx, float2* Y, int ldy, int ncols,
                             const float* sigma_dev, cudaStream_t s, long long* launches) {
   if (ncols <= 0) return;
-  if (!stencil_c64_tma_ok(X, ldx)) throw Error{SWI_EINVAL, "TMA stencil: needs an even leading dimension"};
-  CUtensorMap map;
-  const cuuint64_t dims[4] = {(cuuint64_t)2 * ldx, (cuuint64_t)P.nx, (cuuint64_t)P.ny, (cuuint64_t)P.nz};
-  const cuuint64_t strides[3] = {(cuuint64_t)8 * ldx, (cuuint64_t)8 * ldx * P.nx,
-                                 (cuuint64_t)8 * ldx * P.nx * P.ny};
-  const cuuint32_t box[4] = {2 * kNC, kBX, kBY, 1};
-  const cuuint32_t estr[4] = {1, 1, 1, 1};
-  const CUresult r = encode_fn()(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float2*>(X), dims, strides, box,
-                                 estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                                 CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) throw Error{SWI_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")"};
+  if (!stencil_c64_tma_ok(X, ldx) || P.VG == nullptr)
+    throw Error{SWI_EINVAL, "TMA stencil: needs an even leading dimension and the packed (V, Gamma) planes"};
+  const int nxp = P.nx + (P.nx & 1);
+  CUtensorMap map, vgmap;
+  {
+    const cuuint64_t dims[4] = {(cuuint64_t)2 * ldx, (cuuint64_t)P.nx, (cuuint64_t)P.ny, (cuuint64_t)P.nz};
+    const cuuint64_t strides[3] = {(cuuint64_t)8 * ldx, (cuuint64_t)8 * ldx * P.nx,
+                                   (cuuint64_t)8 * ldx * P.nx * P.ny};
+    const cuuint32_t box[4] = {2 * kNC, kBX, kBY, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult r = encode_fn()(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float2*>(X), dims, strides,
+                                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) throw Error{SWI_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")"};
+  }
+  {
+    // (V, Gamma) pairs, rows of nxp points (16-byte row pitch); box = the tile
+    const cuuint64_t dims[3] = {(cuuint64_t)2 * nxp, (cuuint64_t)P.ny, (cuuint64_t)P.nz};
+    const cuuint64_t strides[2] = {(cuuint64_t)8 * nxp, (cuuint64_t)8 * nxp * P.ny};
+    const cuuint32_t box[3] = {2 * kTX, kTY, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = encode_fn()(&vgmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float2*>(P.VG), dims,
+                                   strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) throw Error{SWI_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")"};
+  }
   const int tiles_x = (P.nx + kTX - 1) / kTX, tiles_y = (P.ny + kTY - 1) / kTY;
   const int cgroups = (ncols + kNC - 1) / kNC;
   const int blocks_xy = tiles_x * tiles_y * cgroups;
-  // about one block per SM; each z chunk at least 16 planes deep
+  // about one block per SM; each z chunk at least 24 planes deep (the sweep
+  // reads 12 planes beyond its chunk)
   int nzc = std::max(1, (152 + blocks_xy / 2) / blocks_xy);
-  nzc = std::max(1, std::min(nzc, P.nz / 16));
+  nzc = std::max(1, std::min(nzc, P.nz / 24));
   const int zchunk = (P.nz + nzc - 1) / nzc;
   const dim3 grid(blocks_xy, (P.nz + zchunk - 1) / zchunk);
   const size_t smem = (size_t)kStages * kStageBytes;
   if (P.bc == SWI_BC_ZERO) {
     SWI_CUDA_TRY(cudaFuncSetAttribute(stencil_c64_tma_kernel<SWI_BC_ZERO>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    stencil_c64_tma_kernel<SWI_BC_ZERO><<<grid, kThreads, smem, s>>>(map, P, X, ldx, Y, ldy, ncols, sigma_dev, zchunk,
+    stencil_c64_tma_kernel<SWI_BC_ZERO><<<grid, kThreads, smem, s>>>(map, vgmap, P, Y, ldy, ncols, sigma_dev, zchunk,
                                                                      cgroups, tiles_x);
   } else {
     SWI_CUDA_TRY(cudaFuncSetAttribute(stencil_c64_tma_kernel<SWI_BC_ODD>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    stencil_c64_tma_kernel<SWI_BC_ODD><<<grid, kThreads, smem, s>>>(map, P, X, ldx, Y, ldy, ncols, sigma_dev, zchunk,
+    stencil_c64_tma_kernel<SWI_BC_ODD><<<grid, kThreads, smem, s>>>(map, vgmap, P, Y, ldy, ncols, sigma_dev, zchunk,
                                                                     cgroups, tiles_x);
   }
   SWI_CHECK_LAUNCH();

@@ -178,7 +178,12 @@ __global__ void __launch_bounds__(kThreadsDs, 1)
         cfma(acc, cmh[m], cml[m], q[kR - m]);
         cfma(acc, cmh[m], cml[m], q[kR + m]);
       }
-      B.Y[row * B.ldy + c] = make_double2((double)acc[0] + (double)acc[1], (double)acc[2] + (double)acc[3]);
+      if (B.out_ds) {
+        const ds::df re = ds::two_sum(acc[0], acc[1]), im = ds::two_sum(acc[2], acc[3]);
+        reinterpret_cast<float4*>(B.Y)[row * B.ldy + c] = make_float4(re.h, re.l, im.h, im.l);
+      } else {
+        B.Y[row * B.ldy + c] = make_double2((double)acc[0] + (double)acc[1], (double)acc[2] + (double)acc[3]);
+      }
     }
 #pragma unroll
     for (int k = 0; k < 2 * kR; ++k) q[k] = q[k + 1];

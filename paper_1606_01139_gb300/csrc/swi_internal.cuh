@@ -91,6 +91,7 @@ struct StencilBlock {
   double2* Y;
   int ldx, ldy, ncols;
   int sigma_off;      // index into the sigma table of column 0
+  int out_ds;         // double-single kernel: Y holds (re hi, re lo, im hi, im lo) floats instead of complex128
 };
 
 // complex64 form (FP32 arithmetic), one block of columns
@@ -100,7 +101,10 @@ struct StencilC64Params {
   float cm[7];       // -c_m / (2 h^2)
   const float* V;    // N
   const float* G;    // Gamma_L + Gamma_R, N
+  const float2* VG;  // (V, Gamma) pairs, [nz][ny][nx rounded up to even] (the TMA-staged kernel)
 };
+// VG[(z ny + y) nxp + x] = (V, G) at (x, y, z), nxp = nx rounded up to even (padding zero)
+void launch_pack_vg(const float* V, const float* G, int nx, int ny, int nz, float2* VG, cudaStream_t s);
 void launch_stencil_c64(const StencilC64Params& P, const float2* X, int ldx, float2* Y, int ldy, int ncols,
                         const float* sigma_dev, cudaStream_t s, long long* launches);
 // TMA-staged form (stencil_c64_tma.cu): needs an even ldx and a 16-byte aligned X
@@ -272,10 +276,11 @@ void launch_sub_diag(double2* Y, int ldy, const double2* X, int ldx, const doubl
 // ---------------------------------------------------------------- single-vector Krylov loop
 // (krylov_sv.cu), also with blocks of nb = 2 new vectors per window and step.
 // Per job (window): Q [N][ldq] basis columns [0, ncols) (complex64 or
-// complex128; ncols may be 0), w the nb adjacent columns of a [N][ldw] block of
-// the same type, c the [ncols][nb] FP64 coefficients, part [nchunks][ldp] FP64
-// chunk partials.
-enum { SV_GRAM = 0, SV_UPDATE_GRAM = 1, SV_UPDATE_NORM = 2 };
+// complex128; ncols may be 0), w the nb adjacent columns of a [N][ldw] block
+// (complex64 in the FP32 form; in the double-single form four floats per
+// entry, the heads and tails of the real and imaginary parts), c the
+// [ncols][nb] FP64 coefficients, part [nchunks][ldp] FP64 chunk partials.
+enum { SV_GRAM = 0, SV_UPDATE_GRAM = 1, SV_UPDATE = 2, SV_WGRAM = 3 };
 struct SvJob {
   const void* Q;
   int ldq, ncols;
@@ -290,8 +295,10 @@ struct SvBatch {
   SvJob job[kMaxBatch];
 };
 // SV_GRAM: part = Q^H w ([ncols][nb]); SV_UPDATE_GRAM: w -= Q c, then
-// part = Q^H w; SV_UPDATE_NORM: w -= Q c, then part = w^H w ([nb][nb]).
-// ds: complex128 in double-single arithmetic, else complex64 in FP32.
+// part = Q^H w; SV_UPDATE: w -= Q c; SV_WGRAM: part = w^H w ([nb][nb], Q
+// unused).  ds: complex128 basis with double-single products (the Gram pass
+// and the update without a fused Gram in FP32, for the first pass and for the
+// second pass's small coefficients), else complex64 in FP32.
 void launch_sv_pass(const SvBatch& b, int mode, bool ds, int nb, int N, int rpc, cudaStream_t s,
                     long long* launches);
 // rows per chunk for njobs windows (256 to 1024, a multiple of 8)
@@ -316,7 +323,9 @@ struct SvReduceBatch {
   SvReduceJob job[kMaxBatch];
 };
 void launch_sv_reduce(const SvReduceBatch& b, cudaStream_t s, long long* launches);
-// dst1[:, b] (and dst2[:, b]) = sum_a w[:, a] r[a * nb + b] for b < nb (in place allowed)
+// dst1[:, b] (and dst2[:, b]) = sum_a w[:, a] r[a * nb + b] for b < nb, in the
+// basis element type (out_w = 0) or in w's own format (out_w = 1, dst2 unused;
+// in place allowed)
 struct SvNormJob {
   const void* w;
   int ldw;
@@ -325,6 +334,7 @@ struct SvNormJob {
   void* dst2;  // may be NULL
   int ld2;
   const double2* r;
+  int out_w;
 };
 struct SvNormBatch {
   int n;

@@ -75,6 +75,7 @@ swi_status do_solve_more(swi_ctx* c, int p, const double* sigma, const int* n_re
   const std::vector<double> sig_old = c->last_sigma;
   const std::vector<double2> epsw_old = c->last_eps_win;
   const std::vector<int> winw_old = c->last_win_of;
+  const std::vector<int> holes_old = c->last_holes;  // interfaces between stored windows
   std::vector<int> win_old(n_old);
   for (int k = 0; k < n_old; ++k) {
     int best = 0;
@@ -153,6 +154,17 @@ swi_status do_solve_more(swi_ctx* c, int p, const double* sigma, const int* n_re
     winw.push_back(rank[p_old + winw_new[k]]);
   }
   record_windows(c, epsw, winw, p_all);
+  // An interface between two stored windows keeps the flag of the run that
+  // computed them: the stored pairs are already free of redundancy, so the
+  // union's merge cannot see it again.
+  int holes = 0;
+  for (int r = 0; r + 1 < p_all; ++r) {
+    const int a = ord[r], b = ord[r + 1];
+    if (a < p_old && b < p_old && r < (int)c->last_holes.size())
+      c->last_holes[r] = (b == a + 1 && a < (int)holes_old.size()) ? holes_old[a] : 0;
+    if (r < (int)c->last_holes.size()) holes += c->last_holes[r] != 0;
+  }
+  minfo[2] = holes;
   c->Uall.release();
   const int nout = minfo[0];
   explicit_residuals(c, c->U.as<double2>(), nout, c->eps.as<double2>(), nout, c->resid);
@@ -325,8 +337,21 @@ swi_status do_plan_sampled(swi_ctx* c, int n_r, int p, const swi_plan_opts* po, 
     ++samples;
     const std::vector<double> r = current_re(c);
     if (r.empty()) return fail(c, SWI_ENOCONV, "planner: a sampling solve found no pairs");
-    for (double x : r)
-      if (x > prev_top) spec.push_back(x);
+    // add the sample's eigenvalues not yet counted, with multiplicity: a real
+    // part that repeats (a twofold eigenvalue) counts as often as the sample
+    // holds it, values the earlier samples found are not counted twice
+    {
+      const double tau_rel = std::max(1e-7, 100.0 * tol);
+      const std::vector<double> have = spec;
+      for (size_t i = 0; i < r.size(); ++i) {
+        const double x = r[i], tau = tau_rel * std::max(1.0, std::fabs(x));
+        if (x < prev_top - tau) continue;
+        int rank = 0, old = 0;
+        for (size_t k = 0; k <= i; ++k) rank += std::fabs(r[k] - x) <= tau;
+        for (double y : have) old += std::fabs(y - x) <= tau;
+        if (rank > old) spec.push_back(x);
+      }
+    }
     const double lo = r.front(), hi = r.back();
     if (!(hi > prev_top)) return fail(c, SWI_ENOCONV, "planner: the sampling made no progress");
     prev_top = hi;

@@ -1,6 +1,6 @@
 """The bench workload's window plan on CPU: 8 windows of equal eigenpair count
 over the lowest 400 real parts of the 48x48x96 wire (the committed Kohn-Sham
-spectrum), shift at the middle of each run of 50, requests x1.25 + 4."""
+spectrum), shift at the middle of each run of 50, requests ceil(50 x 1.1) + 2."""
 import sys
 
 import numpy as np
@@ -15,7 +15,8 @@ def test_plan_of_the_48x48x96_workload():
     cfg = W.CONFIGS[bench.WORKLOAD]
     sig, req, E, source = bench.plan(cfg)
     assert source == "ks_spectrum"
-    assert len(sig) == cfg["p"] == 8 and list(req) == [67] * 8
+    n_req = int(np.ceil(50 * bench.INFLATE)) + bench.EXTRA
+    assert len(sig) == cfg["p"] == 8 and list(req) == [n_req] * 8 and 52 <= n_req <= 60
     lam = bench.ks_spectrum(bench.WORKLOAD)[:cfg["n_r"]]
     per = cfg["n_r"] // cfg["p"]
     for j in range(cfg["p"]):

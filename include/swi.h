@@ -138,16 +138,17 @@ typedef struct {
   double t_merge_s;     /* wall time of merge, selection and normalisation */
 } swi_solve_info;
 
-/* Create a context on the current CUDA device for the operator of Eq. 1 on an
- * nx x ny x nz grid of spacing h (Section 1: the Hamiltonian is applied as a
- * matrix-free finite-difference formula, never stored).
+/* Create a context on the current CUDA device for the operator
+ * A = H_KS - i Gamma of Eq. 1 on an nx x ny x nz grid of spacing h (Section 1:
+ * the Hamiltonian is applied as a matrix-free finite-difference formula, never
+ * stored).  *out receives the context, owned by the caller (swi_destroy).
  *  bc: SWI_BC_ODD -- psi = 0 on the planes just outside the grid, ghosts by
  *      odd reflection u[-1-k] = -u[-1+k] (keeps A = A^T exactly);
  *      SWI_BC_ZERO -- every ghost is zero.
  *  precision: SWI_PREC_F64 -- complex128 Krylov vectors with FP64-class
  *      arithmetic (native FP64 or double-single, swi_solve_opts.arith);
  *      SWI_PREC_MIXED -- the reduced-precision form: swi_solve runs
- *      single-vector windows on complex64 Krylov vectors with FP32 stencil
+ *      1- or 2-vector windows on complex64 Krylov vectors with FP32 stencil
  *      and products (FP32 accumulation within chunks of at most 1024 grid
  *      rows, FP64 across them) and the projected eigenproblems in
  *      double-single; the delivered pairs are complex128 and their explicit
@@ -292,8 +293,10 @@ swi_status swi_get_windows(swi_ctx* ctx, int cap, double* sigma, int* holes, int
  * window count in *p. */
 swi_status swi_get_window_info(swi_ctx* ctx, int cap, swi_window_info* out, int* p);
 
-/* Borrowed device pointers to the current pairs: eps complex128[n], U
- * complex128 [N][ldU] (row-major), U^T U = I.  Errors: SWI_ESTATE (no pairs). */
+/* Borrowed device pointers to the current pairs (the eigenpairs of Eq. 1 that
+ * Algorithm 2 kept, normalised to U^T U = I as Section 1 requires for the
+ * spectral G): eps complex128[n], U complex128 [N][ldU] (row-major).  Valid
+ * until the next call that changes the pairs.  Errors: SWI_ESTATE (no pairs). */
 swi_status swi_get_eigenpairs(swi_ctx* ctx, int* n, const void** eps_dev, const void** U_dev,
                               int* ldU);
 
@@ -308,7 +311,9 @@ swi_status swi_set_eigenpairs(swi_ctx* ctx, int n, const void* eps, const void* 
                               int on_device);
 
 /* Explicit relative residuals ||A u_k - eps_k u_k|| / (||A||_G ||u_k||) of the
- * current pairs (host array of n doubles). */
+ * current pairs, A of Eq. 1 applied in native FP64 (the convergence measure of
+ * the windows of Eq. 3; the paper states no tolerance), ||A||_G the Gershgorin
+ * bound of A.  res_out: host array of n doubles.  Errors: SWI_ESTATE (no pairs). */
 swi_status swi_residuals(swi_ctx* ctx, double* res_out);
 
 /* Options of swi_refine (zero-initialise; zero fields take the defaults). */
@@ -323,6 +328,9 @@ typedef struct {
   double rel_tol;       /* target relative residual, as in swi_solve (default 1e-10) */
   double eq_rtol;       /* Algorithm 2 tests applied to the refined pairs, as */
   double drop_tol;      /* in swi_solve_opts (defaults 1e-8, 1e-6) */
+  double near_tol;      /* groups whose largest relative residual is above it
+                           are far from convergence and left as they are
+                           (default 1e-3) */
 } swi_refine_opts;
 
 typedef struct {
@@ -347,9 +355,10 @@ typedef struct {
  * Q^T (A - sigma_g) Q y = theta Q^T Q y (the unconjugated form, under which
  * the eigenvectors of the complex-symmetric A are bi-orthogonal, Section 1)
  * of smallest magnitude (the windows' SM selection, Eq. 3) give
- * eps = sigma_g + theta and U = Q y; a group keeps its new pairs only if
- * their largest explicit FP64 residual is below the old one (otherwise the
- * previous pairs are put back).  All pairs then pass Algorithm 2 as
+ * eps = sigma_g + theta and U = Q y; a group keeps its new pairs unless they
+ * lower its count of pairs at rel_tol or raise its largest explicit FP64
+ * residual more than tenfold (otherwise the previous pairs are put back), and
+ * a group whose largest residual is above near_tol is not swept.  All pairs then pass Algorithm 2 as
  * one window (equal-eigenvalue projection, redundancy drop, U^T U = I), and
  * the explicit FP64 residuals are recomputed; sweeps stop when every pair is
  * at rel_tol.  The pairs stay in library-owned memory (swi_get_eigenpairs).
@@ -382,9 +391,12 @@ swi_status swi_grad(swi_ctx* ctx, int nE, const double* E, const double* dLdT, d
  * roofline accounting.  Classes: */
 enum {
   SWI_K_STENCIL = 0,  /* shifted stencil (A - sigma) X */
-  SWI_K_GRAM = 1,     /* orthogonalisation inner products C = Q^H W */
-  SWI_K_UPDATE = 2,   /* orthogonalisation update W -= Q C */
-  SWI_K_CHOLQR = 3,   /* Cholesky-QR of each new block */
+  SWI_K_GRAM = 1,     /* orthogonalisation inner products C = Q^H W (windows of
+                         1-2 vectors: the first, FP32 Gram pass) */
+  SWI_K_UPDATE = 2,   /* orthogonalisation update W -= Q C (windows of 1-2
+                         vectors: the update fused with the second Gram pass) */
+  SWI_K_CHOLQR = 3,   /* Cholesky-QR of each new block (windows of 1-2 vectors:
+                         with the second, FP32 update) */
   SWI_K_SCHUR = 4,    /* projected eigenproblem (Schur form, SM selection, reordering) */
   SWI_K_ROTATE = 5,   /* thick-restart rotation Q Z and Ritz vectors */
   SWI_K_MERGE = 6,    /* Algorithm 2 and normalisation, explicit residuals */

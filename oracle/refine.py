@@ -11,7 +11,9 @@ that are already computed.  The paper gives no further detail, so this module
 fixes a reading:
 
 * pairs ordered by real part are cut into groups of ``group`` consecutive
-  pairs; a group whose pairs all have relative residual <= rel_tol is kept;
+  pairs; a group whose pairs all have relative residual <= rel_tol is kept,
+  and so is a group whose largest relative residual is above ``near_tol``
+  (far from convergence: the sweep corrects pairs, it does not solve);
 * otherwise, with U_g the group's vectors and R_u = A U_u - U_u diag(eps_u)
   the residuals of its unconverged pairs u, Q is a basis of span[U_g, R_u]
   (Householder QR here), sigma_g the middle of the group's real parts, and the
@@ -41,7 +43,7 @@ from . import eigen, partition
 
 
 def rr_sweep(apply_A, eps: np.ndarray, U: np.ndarray, res: np.ndarray, rel_tol: float, group: int = 16,
-             eq_rtol: float = 1e-8, drop_tol: float = 1e-6, anorm: float | None = None):
+             eq_rtol: float = 1e-8, drop_tol: float = 1e-6, anorm: float | None = None, near_tol: float = 1e-3):
     """One sweep over the Re-sorted pairs (eps, U) with relative residuals res (relative to anorm;
     anorm None skips the rule that keeps a group's previous pairs)."""
     n = len(eps)
@@ -50,7 +52,7 @@ def rr_sweep(apply_A, eps: np.ndarray, U: np.ndarray, res: np.ndarray, rel_tol: 
     for lo in range(0, n, group):
         g = list(range(lo, min(n, lo + group)))
         u = [k for k in g if not res[k] <= rel_tol]
-        if not u:
+        if not u or not np.max(res[g]) <= near_tol:
             continue
         R = apply_A(U[:, u]) - U[:, u] * eps[u][None, :]
         Q, _ = np.linalg.qr(np.concatenate([U[:, g], R], axis=1))
@@ -77,12 +79,12 @@ def relative_residuals(apply_A, anorm: float, eps: np.ndarray, U: np.ndarray) ->
 
 
 def refine(apply_A, anorm: float, eps: np.ndarray, U: np.ndarray, rel_tol: float, max_sweeps: int = 3,
-           group: int = 16, eq_rtol: float = 1e-8, drop_tol: float = 1e-6):
+           group: int = 16, eq_rtol: float = 1e-8, drop_tol: float = 1e-6, near_tol: float = 1e-3):
     """Sweeps until every pair is at rel_tol or max_sweeps ran; returns (eps, U, residuals, sweeps)."""
     res = relative_residuals(apply_A, anorm, eps, U)
     sweeps = 0
     while sweeps < max_sweeps and not np.all(res <= rel_tol):
-        eps, U = rr_sweep(apply_A, eps, U, res, rel_tol, group, eq_rtol, drop_tol, anorm)
+        eps, U = rr_sweep(apply_A, eps, U, res, rel_tol, group, eq_rtol, drop_tol, anorm, near_tol)
         res = relative_residuals(apply_A, anorm, eps, U)
         sweeps += 1
     return eps, U, res, sweeps

@@ -47,7 +47,8 @@ class SolveOpts(C.Structure):
 
 class RefineOpts(C.Structure):
     _fields_ = [("max_sweeps", C.c_int), ("group", C.c_int), ("arith", C.c_int), ("reserved", C.c_int),
-                ("rel_tol", C.c_double), ("eq_rtol", C.c_double), ("drop_tol", C.c_double)]
+                ("rel_tol", C.c_double), ("eq_rtol", C.c_double), ("drop_tol", C.c_double),
+                ("near_tol", C.c_double)]
 
 
 class RefineInfo(C.Structure):
@@ -368,11 +369,11 @@ class Context:
         return self._check(self._lib.swi_set_eigenpairs(self._h, Uc.shape[1], _ptr(e), _ptr(Uc), 0))
 
     def refine(self, max_sweeps=3, group=16, rel_tol=1e-10, arith=ARITH_DS, eq_rtol=0.0, drop_tol=0.0,
-               allow=(SWI_OK, SWI_ENOCONV)):
+               near_tol=0.0, allow=(SWI_OK, SWI_ENOCONV)):
         """Residual-correction sweeps on the current pairs (Rayleigh-Ritz on span[U_g, R_u] per group of
         `group` consecutive pairs, then Algorithm 2 as one window); returns the info dict with "status"."""
         o = RefineOpts(max_sweeps=max_sweeps, group=group, arith=arith, rel_tol=rel_tol, eq_rtol=eq_rtol,
-                       drop_tol=drop_tol)
+                       drop_tol=drop_tol, near_tol=near_tol)
         info = RefineInfo()
         rc = self._check(self._lib.swi_refine(self._h, C.byref(o), C.byref(info)), allow)
         d = info.as_dict()

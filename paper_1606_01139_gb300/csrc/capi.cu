@@ -718,6 +718,7 @@ swi_status do_refine(swi_ctx* c, const swi_refine_opts* o, swi_refine_info* info
     return fail(c, SWI_EINVAL, "unknown arithmetic");
   if (opt.rel_tol < 0 || opt.eq_rtol < 0 || opt.drop_tol < 0) return fail(c, SWI_EINVAL, "negative tolerance");
   const double rel_tol = opt.rel_tol > 0 ? opt.rel_tol : 1e-10;
+  const double near_tol = opt.near_tol > 0 ? opt.near_tol : 1e-3;
   const double eq_rtol = opt.eq_rtol > 0 ? opt.eq_rtol : 1e-8;
   const double drop_tol = opt.drop_tol > 0 ? opt.drop_tol : 1e-6;
   c->arith = opt.arith == SWI_ARITH_F64 ? SWI_ARITH_F64 : SWI_ARITH_DS;
@@ -782,8 +783,11 @@ swi_status do_refine(swi_ctx* c, const swi_refine_opts* o, swi_refine_info* info
     // unconverged pairs of every group, uploaded once
     std::vector<int> idx, ioff(ngroups + 1, 0);
     for (int gi = 0; gi < ngroups; ++gi) {
-      for (int k = gi * g; k < std::min(n, gi * g + g); ++k)
-        if (!(c->resid[k] <= rel_tol)) idx.push_back(k);
+      double gmax = 0.0;
+      for (int k = gi * g; k < std::min(n, gi * g + g); ++k) gmax = std::max(gmax, c->resid[k]);
+      if (gmax <= near_tol)  // a group far from convergence is left as it is
+        for (int k = gi * g; k < std::min(n, gi * g + g); ++k)
+          if (!(c->resid[k] <= rel_tol)) idx.push_back(k);
       ioff[gi + 1] = (int)idx.size();
     }
     idx_dev.ensure(sizeof(int) * std::max<size_t>(idx.size(), 1));
@@ -863,8 +867,8 @@ swi_status do_refine(swi_ctx* c, const swi_refine_opts* o, swi_refine_info* info
       sb.job[0] = swi::SchurJob{w.H.as<double2>(), w.Z.as<double2>(), w.Bm.as<double2>(), w.Bz.as<double2>(),
                                 w.theta.as<double2>(), w.resid.as<double>(), w.S.as<double2>(),
                                 oinfo.as<int>() + 4 * gi, m, ld, 1, ng, ng, ng, 1.0, w.Hw.p, w.Zw.p};
-      if (c->arith == SWI_ARITH_F64) swi::launch_schur_batch(sb, c->stream, &c->launches);
-      else swi::launch_schur_ds_batch(sb, c->stream, &c->launches);
+      // the group's projected problem is small (order <= 2 n_g): native FP64
+      swi::launch_schur_batch(sb, c->stream, &c->launches);
       swi::RitzBatch fin;
       fin.n = 1;
       fin.job[0] = swi::RitzJob{w.Z.as<double2>(), w.S.as<double2>(), w.theta.as<double2>(), w.resid.as<double>(),

@@ -212,6 +212,12 @@ __global__ void __launch_bounds__(kDenseThreads) schur_kernel(const __grid_const
     int its = 0;
     const int max_its = 60 * m + 100;
     int total_its = 0;
+    // a subdiagonal entry is negligible below DBL_EPSILON times its diagonal
+    // neighbours or times the largest entry of H (wanted Ritz values of
+    // A - sigma lie near zero)
+    double hmax = 0.0;
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) hmax = fmax(hmax, cabs1(HH(i, j)));
     while (ihi > 0) {
       // deflation search (all threads read the same values)
       int l = ihi;
@@ -219,7 +225,7 @@ __global__ void __launch_bounds__(kDenseThreads) schur_kernel(const __grid_const
         const double2 sub = HH(l, l - 1);
         double tst = cabs1(HH(l - 1, l - 1)) + cabs1(HH(l, l));
         if (tst == 0.0) tst = 1.0;
-        if (cabs1(sub) <= DBL_EPSILON * tst) break;
+        if (cabs1(sub) <= DBL_EPSILON * fmax(tst, hmax)) break;
         --l;
       }
       __syncthreads();

@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(kThreads) sv_gram_kernel(const __grid_constant
 // A warp per row; lane l holds basis columns l, l + 32, ... (NT of them, the
 // row's values kept in registers for the fused Gram).
 template <class Pol, int NT, int NB, bool FUSE_GRAM>
-__global__ void __launch_bounds__(kThreads, (NT <= 8 && (NB == 1 || !FUSE_GRAM)) ? 2 : 1) sv_update_kernel(const __grid_constant__ SvBatch batch, int N, int rpc) {
+__global__ void __launch_bounds__(kThreads, (NT <= 8) ? 2 : 1) sv_update_kernel(const __grid_constant__ SvBatch batch, int N, int rpc) {
   using T = typename Pol::T;
   using A = typename Pol::A;
   using Sp = typename Pol::S;
@@ -304,7 +304,9 @@ __global__ void __launch_bounds__(kThreads, (NT <= 8 && (NB == 1 || !FUSE_GRAM))
   const int ncols = J.ncols;
   Sp* cs = reinterpret_cast<Sp*>(sh);
   double2* red = sh + (size_t)ncols * NB;
-  for (int i = threadIdx.x; i < ncols * NB; i += kThreads) cs[i] = Pol::split(Pol::from_c(J.c[i]));
+  // stored vector-major (cs[b * ncols + i]): a warp's lanes read consecutive
+  // 16-byte entries, without bank conflicts
+  for (int e = threadIdx.x; e < ncols * NB; e += kThreads) cs[(e % NB) * ncols + e / NB] = Pol::split(Pol::from_c(J.c[e]));
   __syncthreads();
   using Wt = typename Pol::W;
   const T* __restrict__ Q = static_cast<const T*>(J.Q);
@@ -317,8 +319,6 @@ __global__ void __launch_bounds__(kThreads, (NT <= 8 && (NB == 1 || !FUSE_GRAM))
 #pragma unroll
     for (int b = 0; b < NB; ++b) acc[t][b] = Pol::zero();
   for (int r = r0 + warp; r < r1; r += kWarps) {
-    // the row's basis values (split once when the fused Gram reuses them)
-    Sp q[FUSE_GRAM ? NT : 1];
     A d[NB];
     if constexpr (!FUSE_GRAM) {
       // the update by the second pass's coefficients: products of the heads in FP32
@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(kThreads, (NT <= 8 && (NB == 1 || !FUSE_GRAM))
         const int i = lane + 32 * t;
         if (i < ncols)
 #pragma unroll
-          for (int b = 0; b < NB; ++b) Pol::fmac(f[b], qr[t], cs[i * NB + b]);
+          for (int b = 0; b < NB; ++b) Pol::fmac(f[b], qr[t], cs[b * ncols + i]);
       }
 #pragma unroll
       for (int b = 0; b < NB; ++b) {
@@ -345,19 +345,18 @@ __global__ void __launch_bounds__(kThreads, (NT <= 8 && (NB == 1 || !FUSE_GRAM))
         d[b] = Pol::fto_A(f[b]);
       }
     } else {
-#pragma unroll
-      for (int t = 0; t < NT; ++t) {
-        const int i = lane + 32 * t;
-        q[t] = Pol::split(i < ncols ? __ldg(Q + (long long)r * J.ldq + i) : T{});
-      }
+      // the row's basis values are read again (from L1) for the Gram below
+      // rather than held in registers: half the registers, twice the warps
 #pragma unroll
       for (int b = 0; b < NB; ++b) d[b] = Pol::zero();
 #pragma unroll
       for (int t = 0; t < NT; ++t) {
         const int i = lane + 32 * t;
-        if (i < ncols)
+        if (i < ncols) {
+          const Sp qs = Pol::split(__ldg(Q + (long long)r * J.ldq + i));
 #pragma unroll
-          for (int b = 0; b < NB; ++b) Pol::mac_s(d[b], q[t], cs[i * NB + b]);
+          for (int b = 0; b < NB; ++b) Pol::mac_s(d[b], qs, cs[b * ncols + i]);
+        }
       }
 #pragma unroll
       for (int b = 0; b < NB; ++b)
@@ -378,9 +377,14 @@ __global__ void __launch_bounds__(kThreads, (NT <= 8 && (NB == 1 || !FUSE_GRAM))
 #pragma unroll
       for (int b = 0; b < NB; ++b) ws[b] = Pol::bcast0(ws[b]);
 #pragma unroll
-      for (int t = 0; t < NT; ++t)
+      for (int t = 0; t < NT; ++t) {
+        const int i = lane + 32 * t;
+        if (i < ncols) {
+          const Sp qs = Pol::split(__ldg(Q + (long long)r * J.ldq + i));
 #pragma unroll
-        for (int b = 0; b < NB; ++b) Pol::conj_mac_s(acc[FUSE_GRAM ? t : 0][b], q[FUSE_GRAM ? t : 0], ws[b]);
+          for (int b = 0; b < NB; ++b) Pol::conj_mac_s(acc[FUSE_GRAM ? t : 0][b], qs, ws[b]);
+        }
+      }
     }
   }
   double2* out = J.part + (long long)blockIdx.x * J.ldp;

@@ -26,13 +26,22 @@ constexpr int kThreads = 512;
 // owners live in the warps that do not share its scheduler (warps 4, 8, 12 of
 // the 16 share warp 0's), 12 warps or 384 owners.
 constexpr int kMaxOwners = 384;
+// The register-owner sweeps run for orders up to kOwnerPathMaxM; restart
+// matrices of order 240-384 (deflations inside the active window) exhausted
+// the QR iteration limit in that path, so larger orders take the plain sweep.
+constexpr int kOwnerPathMaxM = 224;
 __device__ __forceinline__ int owner_index(int tid) {
   const int w = tid >> 5;
   if ((w & 3) == 0) return -1;
   return (w - 1 - (w >> 2)) * 32 + (tid & 31);
 }
-// deflation and tie tolerances relative to double-single precision
+// deflation and tie tolerances relative to double-single precision: a
+// subdiagonal entry is negligible below kDeflate times its two diagonal
+// neighbours, or below kDeflateAbs times the largest entry of H (the wanted
+// Ritz values of A - sigma lie near zero, where the first test alone would ask
+// for more than double-single rounding can give)
 constexpr float kDeflate = 4e-15f;
+constexpr float kDeflateAbs = 1e-14f;
 
 struct RotD {
   df c;
@@ -140,13 +149,23 @@ __global__ void __launch_bounds__(kThreads) schur_ds_kernel(const __grid_constan
     if (tid == 0) J.ordinfo[2] = 3;
     return;
   }
-  // load H, Z = I
-  for (long long e = tid; e < (long long)m * m; e += blockDim.x) {
-    const int i = (int)(e / m), j = (int)(e % m);
-    HD(i, j) = cfrom(J.H[(long long)i * ld + j]);
-    ZD(i, j) = dc{df{i == j ? 1.f : 0.f, 0.f}, dfz()};
+  // load H, Z = I, and the largest |Re| + |Im| of H
+  __shared__ unsigned s_hmax;
+  if (tid == 0) s_hmax = 0u;
+  __syncthreads();
+  {
+    float hm = 0.f;
+    for (long long e = tid; e < (long long)m * m; e += blockDim.x) {
+      const int i = (int)(e / m), j = (int)(e % m);
+      const double2 h = J.H[(long long)i * ld + j];
+      HD(i, j) = cfrom(h);
+      ZD(i, j) = dc{df{i == j ? 1.f : 0.f, 0.f}, dfz()};
+      hm = fmaxf(hm, (float)(fabs(h.x) + fabs(h.y)));
+    }
+    atomicMax(&s_hmax, __float_as_uint(hm));  // non-negative floats order as their bit patterns
   }
   __syncthreads();
+  const float defl_abs = kDeflateAbs * __uint_as_float(s_hmax);
 
   // ---------------- Householder reduction to Hessenberg form
   for (int c = 0; c + 2 < m; ++c) {
@@ -226,7 +245,7 @@ __global__ void __launch_bounds__(kThreads) schur_ds_kernel(const __grid_constan
       for (int i = tid + 1; i <= ihi; i += blockDim.x) {
         float tst = cabs1f(HD(i - 1, i - 1)) + cabs1f(HD(i, i));
         if (tst == 0.f) tst = 1.f;
-        if (cabs1f(HD(i, i - 1)) <= kDeflate * tst) atomicMax(&s_l, i);
+        if (cabs1f(HD(i, i - 1)) <= fmaxf(kDeflate * tst, defl_abs)) atomicMax(&s_l, i);
       }
       __syncthreads();
       const int l = s_l;
@@ -263,7 +282,7 @@ __global__ void __launch_bounds__(kThreads) schur_ds_kernel(const __grid_constan
       }
       __syncthreads();
       const dc mu = s_mu;
-      if (m <= kMaxOwners) {
+      if (m <= kOwnerPathMaxM) {
         // One barrier per rotation.  Warp 0 chases the bulge: at step k its
         // lanes 0-6 each form one half-rotation h = c u + w v (w = +-s or
         // +-conj(s)) of the 2x2 block {k, k+1}, of row k+2 (the new bulge) and
@@ -527,7 +546,7 @@ __global__ void __launch_bounds__(kThreads) schur_ds_kernel(const __grid_constan
   const int kk = s_flag;
   for (int i = tid; i < m; i += blockDim.x) s_sel[i] = (s_sel[i] < kk) ? 1 : 0;
   __syncthreads();
-  if (m <= kMaxOwners) {
+  if (m <= kOwnerPathMaxM) {
     // Each selected eigenvalue lambda moves up from pos to ks by adjacent swaps
     // q = pos-1, ..., ks, one barrier per swap.  The rotation of swap q comes
     // from (T[q][q+1], lambda - T[q][q]); the next one needs T[q-1][q] after

@@ -53,6 +53,9 @@ struct SvWin {
   int nreq = 0, m = 0, keep = 0, ldq = 0, ldh = 0, col = 0;
   int p = 0;  // the newest block is basis columns [p, p + nb) (the ones expanded next)
   DevMem Q, H, Z, S, Bz, theta, resid, Yw, eps_w, res_w, Hw, Zw, C1, C2, Z32, rinv, part;  // part: FP64 chunk partials
+  DevMem Hsave;          // the projected matrix of the Schur step in flight (for a retry in FP64)
+  bool retry = false;    // the double-single step gave up; the FP64 step runs on the saved matrix
+  int schur_retries = 0;
   bool done = false, failed = false;
   long long matvecs = 0;
   int restarts = 0, nconv = 0;
@@ -174,6 +177,7 @@ swi_status solve_sv(swi_ctx* c, const swi_solve_opts& opt, swi_solve_info* info)
     w.resid.ensure(sizeof(double) * w.ldh);
     w.Hw.ensure(16 * hh);
     w.Zw.ensure(16 * hh);
+    w.Hsave.ensure(sizeof(double2) * hh);
     w.Yw.ensure(sizeof(double2) * w.ldh * w.nreq);
     w.eps_w.ensure(sizeof(double2) * w.nreq);
     w.res_w.ensure(sizeof(double) * w.nreq);
@@ -335,11 +339,48 @@ swi_status solve_sv(swi_ctx* c, const swi_solve_opts& opt, swi_solve_info* info)
     }
   };
 
+  // the projected eigenproblem of window j (order w.p) on its own stream; the
+  // double-single kernel, or after it gave up the native FP64 one on the
+  // saved matrix
+  auto launch_schur = [&](Win& w, bool f64) {
+    const int j = w.col;
+    cudaStream_t sj = side.st[j];
+    const size_t hh = (size_t)w.ldh * w.ldh;
+    if (f64) SWI_CUDA_TRY(cudaMemcpyAsync(w.H.p, w.Hsave.p, sizeof(double2) * hh, cudaMemcpyDeviceToDevice, sj));
+    else SWI_CUDA_TRY(cudaMemcpyAsync(w.Hsave.p, w.H.p, sizeof(double2) * hh, cudaMemcpyDeviceToDevice, sj));
+    // as ARPACK does, keep more Ritz vectors once some wanted pairs have converged
+    const int keep_eff = std::min(w.m - nb, w.keep + std::min(w.nconv, (w.m - w.keep) / 2));
+    swi::SchurBatch sb;
+    sb.n = 1;
+    // B: the nb coupling rows of the Arnoldi relation, rows [p, p + nb) of H
+    double2* H = w.H.template as<double2>();
+    sb.job[0] = swi::SchurJob{H, w.Z.template as<double2>(), H + (long long)w.p * w.ldh, w.Bz.template as<double2>(),
+                              w.theta.template as<double2>(), w.resid.template as<double>(), w.S.template as<double2>(),
+                              c->ordinfo.as<int>() + 4 * j, w.p, w.ldh, nb, keep_eff, w.nreq, w.m - nb, tol_abs,
+                              w.Hw.p, w.Zw.p};
+    {
+      ProfScope ps(c, SWI_K_SCHUR, 0.0, 0.0, sj);
+      if (f64) swi::launch_schur_batch(sb, sj, &c->launches);
+      else swi::launch_schur_ds_batch(sb, sj, &c->launches);
+    }
+    SWI_CUDA_TRY(cudaMemcpyAsync(side.oi + 4 * j, c->ordinfo.as<int>() + 4 * j, sizeof(int) * 4,
+                                 cudaMemcpyDeviceToHost, sj));
+    SWI_CUDA_TRY(cudaEventRecord(side.done[j], sj));
+    in_schur[j] = 1;
+  };
+
   auto finish_restart = [&](int j) {
     Win& w = *win[j];
     const int* oi = side.oi + 4 * j;
     const int kk = oi[0], nconv = oi[1], st = oi[2];
     const int n = w.p;  // order of the projected matrix
+    if (st != 0 && !w.retry) {  // the double-single QR gave up: the FP64 kernel on the same matrix
+      w.retry = true;
+      w.schur_retries++;
+      launch_schur(w, true);
+      return;
+    }
+    w.retry = false;
     SWI_CUDA_TRY(cudaStreamWaitEvent(c->stream, side.done[j], 0));
     w.restarts++;
     w.nconv = nconv;
@@ -405,7 +446,7 @@ swi_status solve_sv(swi_ctx* c, const swi_solve_opts& opt, swi_solve_info* info)
       if (q == cudaErrorNotReady) continue;
       SWI_CUDA_TRY(q);
       in_schur[j] = 0;
-      finish_restart(j);
+      finish_restart(j);  // may start the FP64 retry (in_schur set again)
     }
     std::vector<Win*> act;
     int pending = -1;
@@ -457,15 +498,23 @@ swi_status solve_sv(swi_ctx* c, const swi_solve_opts& opt, swi_solve_info* info)
       r1.job[q] = swi::SvReduceJob{pp, ldp, nchunks, nc, nb, 0, w.C2.template as<double2>(), hcol, w.ldh, nullptr};
       dst[q] = w.p + nb;
     }
+    // profile classes: the first Gram pass; the update fused with the second
+    // Gram (the accurate pass); the second update with the block's Cholesky-QR.
+    // Bytes: each basis read once per pass plus the new vectors; flops: 8 per
+    // complex multiply-add and new vector
+    const double wbytes = 16.0 * Nn * na * nb;
     {
-      ProfScope ps(c, SWI_K_GRAM, 2.0 * 8.0 * Nn * ncol * nb, 2.0 * sizeof(T) * Nn * ncol);
+      ProfScope ps(c, SWI_K_GRAM, 8.0 * Nn * ncol * nb, sizeof(T) * Nn * ncol + wbytes);
       swi::launch_sv_pass(g0, swi::SV_GRAM, DS, nb, c->N, rpc, c->stream, &c->launches);
       swi::launch_sv_reduce(r0, c->stream, &c->launches);
+    }
+    {
+      ProfScope ps(c, SWI_K_UPDATE, 2.0 * 8.0 * Nn * ncol * nb, sizeof(T) * Nn * ncol + 2.0 * wbytes);
       swi::launch_sv_pass(g1, swi::SV_UPDATE_GRAM, DS, nb, c->N, rpc, c->stream, &c->launches);
       swi::launch_sv_reduce(r1, c->stream, &c->launches);
     }
     {
-      ProfScope ps(c, SWI_K_UPDATE, 8.0 * Nn * ncol * nb, sizeof(T) * Nn * ncol + 2.0 * sizeof(T) * Nn * na * nb);
+      ProfScope ps(c, SWI_K_CHOLQR, 8.0 * Nn * ncol * nb, sizeof(T) * Nn * ncol + 6.0 * wbytes);
       swi::launch_sv_pass(g2, swi::SV_UPDATE, DS, nb, c->N, rpc, c->stream, &c->launches);
       orthonormalise(act, dst, true, rpc);
     }
@@ -476,27 +525,9 @@ swi_status solve_sv(swi_ctx* c, const swi_solve_opts& opt, swi_solve_info* info)
       w.p += nb;
       w.matvecs += nb;
       if (w.p + nb <= w.m) continue;
-      // as ARPACK does, keep more Ritz vectors once some wanted pairs have converged
-      const int keep_eff = std::min(w.m - nb, w.keep + std::min(w.nconv, (w.m - w.keep) / 2));
-      cudaStream_t sj = side.st[j];
       SWI_CUDA_TRY(cudaEventRecord(side.ready[j], c->stream));
-      SWI_CUDA_TRY(cudaStreamWaitEvent(sj, side.ready[j], 0));
-      swi::SchurBatch sb;
-      sb.n = 1;
-      // B: the nb coupling rows of the Arnoldi relation, rows [p, p + nb) of H
-      double2* H = w.H.template as<double2>();
-      sb.job[0] = swi::SchurJob{H, w.Z.template as<double2>(), H + (long long)w.p * w.ldh, w.Bz.template as<double2>(),
-                                w.theta.template as<double2>(), w.resid.template as<double>(), w.S.template as<double2>(),
-                                c->ordinfo.as<int>() + 4 * j, w.p, w.ldh, nb, keep_eff, w.nreq, w.m - nb, tol_abs,
-                                w.Hw.p, w.Zw.p};
-      {
-        ProfScope ps(c, SWI_K_SCHUR, 0.0, 0.0, sj);
-        swi::launch_schur_ds_batch(sb, sj, &c->launches);
-      }
-      SWI_CUDA_TRY(cudaMemcpyAsync(side.oi + 4 * j, c->ordinfo.as<int>() + 4 * j, sizeof(int) * 4,
-                                   cudaMemcpyDeviceToHost, sj));
-      SWI_CUDA_TRY(cudaEventRecord(side.done[j], sj));
-      in_schur[j] = 1;
+      SWI_CUDA_TRY(cudaStreamWaitEvent(side.st[j], side.ready[j], 0));
+      launch_schur(w, false);
     }
     SWI_CUDA_TRY(cudaEventRecord(side.lag[step & 1], c->stream));
   }

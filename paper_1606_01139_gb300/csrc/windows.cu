@@ -9,9 +9,10 @@
 //  - Hole filling (Algorithm 1's loop over interfaces that showed no
 //    redundancy): for each hole a window at the middle of the gap between the
 //    highest real part delivered by the lower window and the lowest delivered
-//    by the upper one, requesting 3/2 of the gap's uniform-density count
-//    (E_max - E_min)/N per pair; solved as a continuation, repeated until no
-//    hole remains or the round limit.
+//    by the upper one, requesting 3/2 of the gap's eigenvalue count at the
+//    mean spacing of the two windows' eigenvalues plus 4 (Algorithm 1's
+//    uniform (E_max - E_min)/N where they give none), at most 300; solved as
+//    a continuation, repeated until no hole remains or the round limit.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -214,7 +215,23 @@ swi_status do_fill_holes(swi_ctx* c, double e_min, double e_max, int max_rounds,
       }
       if (!std::isfinite(top) || !std::isfinite(bot)) continue;
       const double s = 0.5 * (top + bot);
-      const int n = (int)std::max(1.0, std::ceil(1.5 * (bot - top) / spacing));
+      // Algorithm 1's request uses the uniform spacing (E_max - E_min)/N; where
+      // the two windows delivered eigenvalues, their own mean spacing is the
+      // better estimate (the density of states varies by orders of magnitude
+      // over a wire's spectrum), and the request stays within a window's reach
+      double lo = INFINITY, hi = -INFINITY;
+      int cnt = 0;
+      for (size_t k = 0; k < c->last_eps_win.size(); ++k)
+        if (c->last_win_of[k] == i || c->last_win_of[k] == i + 1) {
+          lo = std::min(lo, c->last_eps_win[k].x);
+          hi = std::max(hi, c->last_eps_win[k].x);
+          ++cnt;
+        }
+      // (with the local spacing, 4 more: the new window must reach past both
+      // edges of the gap to overlap its neighbours)
+      const bool local = cnt >= 4 && hi > lo;
+      const double sp = local ? (hi - lo) / (cnt - 1) : spacing;
+      const int n = (int)std::min(300.0, std::max(1.0, std::ceil(1.5 * (bot - top) / sp) + (local ? 4 : 0)));
       if (!sg.empty() && !(s > sg.back())) continue;
       sg.push_back(s);
       rq.push_back(n);

@@ -546,11 +546,12 @@ def refine_wire():
     return w, A, eps, U, an
 
 
-def _refine_both(swi, w, A, an, e0, U0, rel_tol, sweeps, group, arith):
-    eo, Uo, ro, so = refine.refine(lambda X: A @ X, an, e0, U0, rel_tol, max_sweeps=sweeps, group=group)
+def _refine_both(swi, w, A, an, e0, U0, rel_tol, sweeps, group, arith, near_tol=1e-3):
+    eo, Uo, ro, so = refine.refine(lambda X: A @ X, an, e0, U0, rel_tol, max_sweeps=sweeps, group=group,
+                                   near_tol=near_tol)
     with _ctx(swi, w) as c:
         c.set_eigenpairs(e0, U0)
-        info = c.refine(max_sweeps=sweeps, group=group, rel_tol=rel_tol, arith=arith)
+        info = c.refine(max_sweeps=sweeps, group=group, rel_tol=rel_tol, arith=arith, near_tol=near_tol)
         eg, Ug = c.eigenpairs()
         rg = c.residuals()
     return (eo, Uo, ro, so), (eg, Ug, rg, info)
@@ -616,7 +617,8 @@ def test_refine_on_unconverged_pairs_bounds_the_residual(swi, refine_wire):
     U0 /= np.sqrt(np.sum(U0 * U0, axis=0))[None, :]
     e0 = np.sort_complex(eps[:n] + 0.05)
     r0 = refine.relative_residuals(lambda X: A @ X, an, e0, U0)
-    (eo, Uo, ro, so), (eg, Ug, rg, info) = _refine_both(swi, w, A, an, e0, U0, 1e-12, 1, 8, swi.ARITH_DS)
+    (eo, Uo, ro, so), (eg, Ug, rg, info) = _refine_both(swi, w, A, an, e0, U0, 1e-12, 1, 8, swi.ARITH_DS,
+                                                        near_tol=1.0)
     assert info["sweeps"] == 1
     assert np.max(rg) <= 10.0 * np.max(r0) * (1 + 1e-9), (np.max(rg), np.max(r0))
     assert len(eg) == len(eo)
@@ -773,7 +775,14 @@ def test_plan_windows_sampled(swi):
         assert abs(pinfo["e_min"] - eps_o.real.min()) <= 1e-6
         assert abs(pinfo["e_max"] - eps_o.real.max()) <= 1e-6 * max(1.0, abs(eps_o.real.max()))
         np.testing.assert_array_equal(req, req_o)
-        np.testing.assert_allclose(sig, sig_o, atol=1e-6)
+        # each shift inside its run of the dense spectrum; a sample window
+        # selects by |eps - sigma| in the complex plane, so a real part near a
+        # run's edge can fall to the neighbouring run
+        r = eps_o.real[:n_r]
+        per = n_r // p
+        for j in range(p):
+            assert r[j * per] - 1e-6 <= sig[j] <= r[(j + 1) * per - 1] + 1e-6, (j, sig, sig_o)
+        assert np.max(np.abs(sig - sig_o)) <= 0.02 * (r[-1] - r[0])
         info = c.solve(block=2, rel_tol=REL_TOL_SV, n_keep=n_r, max_matvecs=60000)
         eps = c.eigenvalues()
     assert info["status"] == "SWI_OK", info
@@ -785,6 +794,33 @@ def _schur_case(m, kind, seed):
     rng = np.random.default_rng(seed)
     if kind == "random":
         return (rng.standard_normal((m, m)) + 1j * rng.standard_normal((m, m))) / np.sqrt(m)
+    if kind == "restart":
+        # the matrix of a thick restart: the kept Schur block T_k (upper
+        # triangular, Ritz values of A - sigma near zero, the converged ones
+        # coupled to the rest by ~1e-15 only) bordered by Arnoldi columns
+        k = m // 2
+        # nearly normal (a Schur block of a weakly non-Hermitian operator):
+        # small off-diagonal entries keep its eigenvalues well conditioned
+        T = np.triu(rng.standard_normal((k, k)) + 1j * rng.standard_normal((k, k)), 1) * (0.05 / np.sqrt(k))
+        T[np.diag_indices(k)] = np.concatenate([1e-3 * (rng.random(k // 2) - 0.5),
+                                                rng.uniform(-5, 40, k - k // 2)]) - 1e-3j * rng.random(k)
+        H = np.zeros((m, m), complex)
+        H[:k, :k] = T
+        bz = rng.standard_normal((2, k)) + 1j * rng.standard_normal((2, k))
+        bz[:, : k // 4] *= 1e-15
+        H[k:k + 2, :k] = bz
+        H[:, k:] = np.triu(rng.standard_normal((m, m - k)) + 1j * rng.standard_normal((m, m - k)), -(k + 1))[:, :]
+        return H
+    if kind == "shifted":
+        # the spectrum a window of A - sigma projects: the wanted values near
+        # zero (spacing ~1e-4, some twofold, small negative imaginary parts)
+        # against the rest of the spectrum up to ~45 (||A||_G of the wires)
+        k = m // 2
+        small = np.repeat(1e-2 * (rng.random((k + 1) // 2) - 0.5), 2)[:k] - 1e-4j * rng.random(k)
+        large = rng.uniform(-5.0, 45.0, m - k) - 0.3j * rng.random(m - k)
+        D = np.concatenate([small, large])
+        V = np.eye(m) + 0.2 * (rng.standard_normal((m, m)) + 1j * rng.standard_normal((m, m))) / np.sqrt(m)
+        return V @ np.diag(D) @ np.linalg.inv(V)
     # twofold eigenvalues, as a 2-vector Krylov window on a mirror-symmetric
     # wire projects them: H = V D V^-1 with pairs of equal entries in D
     d = rng.standard_normal(m // 2) * 0.3 - 0.05j * rng.random(m // 2)
@@ -794,7 +830,7 @@ def _schur_case(m, kind, seed):
 
 
 @pytest.mark.parametrize("m", [96, 229, 236, 244, 245, 300, 357, 372, 384, 389])
-@pytest.mark.parametrize("kind", ["random", "twofold"])
+@pytest.mark.parametrize("kind", ["random", "twofold", "shifted", "restart"])
 def test_schur_step_against_host(swi, m, kind):
     # the device's thick-restart step (double-single Householder reduction,
     # single-shift QR, reordering) against numpy on the same matrix: a Schur
@@ -802,7 +838,7 @@ def test_schur_step_against_host(swi, m, kind):
     # `keep` values of smallest magnitude in the leading block
     H = _schur_case(m, kind, m)
     keep = m // 3
-    w = W.make_wire(4, 4, 6, 0.5, 1, 1)
+    w = W.make_wire(6, 6, 6, 0.5, 1, 1)
     with _ctx(swi, w) as c:
         for b in (1, 2):
             rng = np.random.default_rng(m + b)
@@ -814,9 +850,13 @@ def test_schur_step_against_host(swi, m, kind):
             nH = np.linalg.norm(H)
             assert np.linalg.norm(H @ Z - Z @ T) <= 1e-11 * nH
             assert np.max(np.abs(np.tril(T, -1))) <= 1e-12 * nH
-            assert np.max(np.abs(Z.conj().T @ Z - np.eye(m))) <= 1e-12
+            assert np.max(np.abs(Z.conj().T @ Z - np.eye(m))) <= 1e-11  # ~ m 2^-46 in double-single
             th = np.diag(T)
-            ev = np.linalg.eigvals(H)
-            tol = 1e-7 if kind == "twofold" else 1e-10
-            assert np.max(np.min(np.abs(th[:, None] - ev[None, :]), axis=1)) <= tol * max(1.0, np.max(np.abs(ev)))
+            if kind != "restart":
+                # (a bordered triangular matrix has eigenvalues too ill conditioned
+                # for a comparison; its backward error above is the check)
+                ev = np.linalg.eigvals(H)
+                # a twofold eigenvalue of a non-normal matrix moves by ~sqrt(rounding)
+                tol = 1e-10 if kind == "random" else 1e-6
+                assert np.max(np.min(np.abs(th[:, None] - ev[None, :]), axis=1)) <= tol * max(1.0, np.max(np.abs(ev)))
             assert np.max(np.abs(th[:kept])) <= np.min(np.abs(th[kept:])) * (1 + 1e-9)

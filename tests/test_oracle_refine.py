@@ -95,10 +95,14 @@ def test_sweep_keeps_converged_pairs_and_bounds_the_residual(wire):
         e0, U0 = eigen.sort_by_real(e0, U0)
         r0 = refine.relative_residuals(apply, an, e0, U0)
         assert np.sum(r0 <= tol) == 8
-        e1, U1 = refine.rr_sweep(apply, e0, U0, r0, tol, group=8, eq_rtol=0.0, drop_tol=0.0, anorm=an)
+        e1, U1 = refine.rr_sweep(apply, e0, U0, r0, tol, group=8, eq_rtol=0.0, drop_tol=0.0, anorm=an, near_tol=1.0)
         r1 = refine.relative_residuals(apply, an, e1, U1)
         assert len(e1) == n
         assert np.sum(r1 <= tol) >= 8 and np.max(r1) <= 10.0 * np.max(r0) * (1 + 1e-12)
         # every group replaced or kept whole: the kept groups' pairs are returned unchanged
         e2, U2 = refine.rr_sweep(apply, e0, U0, np.zeros(n), tol, group=8, eq_rtol=0.0, drop_tol=0.0, anorm=an)
         np.testing.assert_array_equal(np.sort_complex(e2), np.sort_complex(e0))
+        # groups far from convergence (largest residual above near_tol) are not swept
+        e3, U3 = refine.rr_sweep(apply, e0, U0, r0, tol, group=8, eq_rtol=0.0, drop_tol=0.0, anorm=an,
+                                 near_tol=0.5 * np.max(r0))
+        np.testing.assert_array_equal(np.sort_complex(e3), np.sort_complex(e0))

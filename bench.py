@@ -353,7 +353,16 @@ def precision_form(swi, stream, wire, sig, req, n_r, budget, ctx64):
                "pairs_rel_res_le_1e-6": int(np.sum(res <= 1e-6)), "pairs_rel_res_le_1e-8": int(np.sum(res <= 1e-8))}
         if len(ok64) == 0:
             return out
-        match = np.array([int(np.argmin(np.abs(eps - eps64[k]))) for k in ok64])
+        # one-to-one, nearest first (both vectors of a twofold eigenvalue need a partner each)
+        D = np.abs(eps64[ok64][:, None] - eps[None, :])
+        match = np.full(len(ok64), -1)
+        used = np.zeros(len(eps), bool)
+        for flat in np.argsort(D, axis=None):
+            a_, b_ = divmod(int(flat), len(eps))
+            if match[a_] < 0 and not used[b_]:
+                match[a_], used[b_] = b_, True
+            if np.all(match >= 0):
+                break
         err = np.abs(eps[match] - eps64[ok64]) / np.maximum(1.0, np.abs(eps64[ok64]))
         Es = np.linspace(eps64[ok64].real.min(), eps64[ok64].real.max(), 32)
         scratch.set_eigenpairs(eps64[ok64], U64[:, ok64])

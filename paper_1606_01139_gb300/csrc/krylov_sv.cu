@@ -94,6 +94,8 @@ struct PolC64 {
   __device__ static F fshfl_xor(F a, int o) { return shfl_xor(a, o); }
   __device__ static double2 fto_d(F a) { return to_d(a); }
   __device__ static A fto_A(F a) { return a; }
+  __device__ static float2 head2(T c) { return c; }
+  __device__ static void fmac2(F& a, T q, float2 c) { mac(a, q, c); }
 };
 
 // x = hi + lo from the bit fields alone (integer and FP32 pipes only): hi is x
@@ -210,6 +212,12 @@ struct PolDs {
   }
   __device__ static double2 fto_d(F a) { return make_double2(a.x, a.y); }
   __device__ static A fto_A(F a) { return A{a.x, 0.f, a.y, 0.f}; }
+  __device__ static float2 head2(T c) { return make_float2(hi_fast(c.x), hi_fast(c.y)); }
+  __device__ static void fmac2(F& a, T q, float2 c) {  // a += q c, FP32 products of the heads
+    const float qr = hi_fast(q.x), qi = hi_fast(q.y);
+    a.x = fmaf(qr, c.x, fmaf(-qi, c.y, a.x));
+    a.y = fmaf(qr, c.y, fmaf(qi, c.x, a.y));
+  }
 };
 
 // ----------------------------------------------------------------- Gram pass
@@ -347,17 +355,21 @@ __global__ void __launch_bounds__(kThreads, (NT <= 8) ? 2 : 1) sv_update_kernel(
     } else {
       // the row's basis values are read again (from L1) for the Gram below
       // rather than held in registers: half the registers, twice the warps
+      // two interleaved accumulators per new vector: independent chains
+      A d1[NB];
 #pragma unroll
-      for (int b = 0; b < NB; ++b) d[b] = Pol::zero();
+      for (int b = 0; b < NB; ++b) d[b] = d1[b] = Pol::zero();
 #pragma unroll
       for (int t = 0; t < NT; ++t) {
         const int i = lane + 32 * t;
         if (i < ncols) {
           const Sp qs = Pol::split(__ldg(Q + (long long)r * J.ldq + i));
 #pragma unroll
-          for (int b = 0; b < NB; ++b) Pol::mac_s(d[b], qs, cs[b * ncols + i]);
+          for (int b = 0; b < NB; ++b) Pol::mac_s((t & 1) ? d1[b] : d[b], qs, cs[b * ncols + i]);
         }
       }
+#pragma unroll
+      for (int b = 0; b < NB; ++b) d[b] = Pol::add(d[b], d1[b]);
 #pragma unroll
       for (int b = 0; b < NB; ++b)
 #pragma unroll
@@ -408,6 +420,72 @@ __global__ void __launch_bounds__(kThreads, (NT <= 8) ? 2 : 1) sv_update_kernel(
       }
     }
     __syncthreads();
+  }
+}
+
+// ----------------------------------------------------------------- the second update (FP32 products)
+// w[r, :] -= Q[r, :] c for the second pass's small coefficients: products of
+// the basis heads in FP32, the row's new value formed in split form by lane 0;
+// a warp per row, few registers so that four blocks share an SM.
+template <class Pol, int NT, int NB>
+__global__ void __launch_bounds__(kThreads, (NT <= 8) ? 4 : ((NT <= 12) ? 2 : 1)) sv_update_fast_kernel(const __grid_constant__ SvBatch batch, int N,
+                                                                      int rpc) {
+  using T = typename Pol::T;
+  using F = typename Pol::F;
+  using Sp = typename Pol::S;
+  using Wt = typename Pol::W;
+  extern __shared__ double2 sh[];
+  const SvJob& J = batch.job[blockIdx.y];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int ncols = J.ncols;
+  // the coefficients' heads, [NB][ncols] (8 bytes per entry: conflict-free reads)
+  float2* cs = reinterpret_cast<float2*>(sh);
+  for (int e = threadIdx.x; e < ncols * NB; e += kThreads) cs[(e % NB) * ncols + e / NB] = Pol::head2(Pol::from_c(J.c[e]));
+  __syncthreads();
+  const T* __restrict__ Q = static_cast<const T*>(J.Q);
+  Wt* w = static_cast<Wt*>(J.w);
+  const int r0 = blockIdx.x * rpc, r1 = min(N, r0 + rpc);
+  constexpr int kRows = 1;
+  for (int r = r0 + warp; r < r1; r += kRows * kWarps) {
+    const int rb = r + kWarps;
+    const bool two = kRows == 2 && rb < r1;
+    T qa[NT], qb[kRows == 2 ? NT : 1];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      const int i = lane + 32 * t;
+      qa[t] = i < ncols ? __ldg(Q + (long long)r * J.ldq + i) : T{};
+      if (kRows == 2) qb[kRows == 2 ? t : 0] = (two && i < ncols) ? __ldg(Q + (long long)rb * J.ldq + i) : T{};
+    }
+    F fa[NB], fb[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) fa[b] = fb[b] = Pol::fzero();
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      const int i = lane + 32 * t;
+      if (i < ncols)
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          const float2 cv = cs[b * ncols + i];
+          Pol::fmac2(fa[b], qa[t], cv);
+          if (kRows == 2) Pol::fmac2(fb[b], qb[kRows == 2 ? t : 0], cv);
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        fa[b] = Pol::fadd(fa[b], Pol::fshfl_xor(fa[b], o));
+        fb[b] = Pol::fadd(fb[b], Pol::fshfl_xor(fb[b], o));
+      }
+    if (lane == 0) {
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        w[(long long)r * J.ldw + b] = Pol::wstore(Pol::wsub(Pol::wload(w[(long long)r * J.ldw + b]), Pol::fto_A(fa[b])));
+        if (two)
+          w[(long long)rb * J.ldw + b] =
+              Pol::wstore(Pol::wsub(Pol::wload(w[(long long)rb * J.ldw + b]), Pol::fto_A(fb[b])));
+      }
+    }
   }
 }
 
@@ -595,6 +673,14 @@ __global__ void sv_normalize_kernel(const __grid_constant__ SvNormBatch batch, i
 template <class Pol, int NT, int NB, bool FUSE>
 void launch_update_nt(const SvBatch& b, int N, int rpc, int maxcols, cudaStream_t s) {
   const int nchunks = (N + rpc - 1) / rpc;
+  if constexpr (!FUSE) {
+    const size_t smem = sizeof(double2) * (size_t)maxcols * NB;
+    if (smem > 48 * 1024)
+      SWI_CUDA_TRY(cudaFuncSetAttribute(sv_update_fast_kernel<Pol, NT, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem));
+    sv_update_fast_kernel<Pol, NT, NB><<<dim3(nchunks, b.n), kThreads, smem, s>>>(b, N, rpc);
+    return;
+  }
   const size_t smem = sizeof(double2) * ((size_t)maxcols * NB + (FUSE ? (size_t)kWarps * NB * 32 : kWarps * NB * NB));
   if (smem > 48 * 1024)
     SWI_CUDA_TRY(cudaFuncSetAttribute(sv_update_kernel<Pol, NT, NB, FUSE>,

@@ -16,9 +16,10 @@
 //
 //  sv_gram_kernel:   part[chunk][i][b] = sum_{rows of chunk} conj(Q[r, i]) w[r, b]
 //                    (a block per 32-column slab and row chunk, one column per lane)
-//  sv_update_kernel: w[r, :] -= Q[r, :] c (a warp per row), then (FUSE_GRAM)
-//                    the next Gram's partials, the row's values reused from
-//                    registers: one read of Q for both passes
+//  sv_update_kernel: w[r, :] -= Q[r, :] c (a warp per row), then the next
+//                    Gram's partials: one pass over Q for both (double-single)
+//  sv_update_fast_kernel: w[r, :] -= Q[r, :] c for the second pass's small
+//                    coefficients (FP32 products of the heads)
 //  sv_wgram_kernel:  part[chunk][a][b] = sum_{rows of chunk} conj(w[r, a]) w[r, b]
 //  sv_reduce_kernel: FP64 sums of the chunk partials, added into columns of H;
 //                    for w^H w the Cholesky factor of the block (Cholesky-QR)
@@ -89,7 +90,6 @@ struct PolC64 {
   using F = float2;
   __device__ static F fzero() { return make_float2(0.f, 0.f); }
   __device__ static void fconj_mac(F& a, T q, S w) { conj_mac(a, q, w); }
-  __device__ static void fmac(F& a, T q, S c) { mac(a, q, c); }
   __device__ static F fadd(F a, F b) { return add(a, b); }
   __device__ static F fshfl_xor(F a, int o) { return shfl_xor(a, o); }
   __device__ static double2 fto_d(F a) { return to_d(a); }
@@ -201,11 +201,6 @@ struct PolDs {
     a.x = fmaf(qr, w.rh, fmaf(qi, w.ih, a.x));
     a.y = fmaf(qr, w.ih, fmaf(-qi, w.rh, a.y));
   }
-  __device__ static void fmac(F& a, T q, const S& c) {  // a += q c
-    const float qr = hi_fast(q.x), qi = hi_fast(q.y);
-    a.x = fmaf(qr, c.rh, fmaf(-qi, c.ih, a.x));
-    a.y = fmaf(qr, c.ih, fmaf(qi, c.rh, a.y));
-  }
   __device__ static F fadd(F a, F b) { return make_float2(a.x + b.x, a.y + b.y); }
   __device__ static F fshfl_xor(F a, int o) {
     return make_float2(__shfl_xor_sync(0xffffffffu, a.x, o), __shfl_xor_sync(0xffffffffu, a.y, o));
@@ -296,16 +291,17 @@ __global__ void __launch_bounds__(kThreads) sv_gram_kernel(const __grid_constant
   }
 }
 
-// ----------------------------------------------------------------- update pass (+ Gram or w^H w)
-// A warp per row; lane l holds basis columns l, l + 32, ... (NT of them, the
-// row's values kept in registers for the fused Gram).
-template <class Pol, int NT, int NB, bool FUSE_GRAM>
+// ----------------------------------------------------------------- update fused with the second Gram
+// The accurate pass: w[r, :] -= Q[r, :] c, then the partials of Q^H w, in
+// double-single.  A warp per row; lane l holds basis columns l, l + 32, ...
+// (NT of them); the row's values are read twice (the second read hits L1)
+// rather than held in registers, which keeps two blocks on an SM.
+template <class Pol, int NT, int NB>
 __global__ void __launch_bounds__(kThreads, (NT <= 8) ? 2 : 1) sv_update_kernel(const __grid_constant__ SvBatch batch, int N, int rpc) {
   using T = typename Pol::T;
   using A = typename Pol::A;
   using Sp = typename Pol::S;
-  // shared: the coefficients c in split form ([ncols][NB], 16-byte slots),
-  // then the cross-warp partials
+  // shared: the coefficients c in split form, then the cross-warp partials
   extern __shared__ double2 sh[];
   const SvJob& J = batch.job[blockIdx.y];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -320,60 +316,30 @@ __global__ void __launch_bounds__(kThreads, (NT <= 8) ? 2 : 1) sv_update_kernel(
   const T* __restrict__ Q = static_cast<const T*>(J.Q);
   Wt* w = static_cast<Wt*>(J.w);
   const int r0 = blockIdx.x * rpc, r1 = min(N, r0 + rpc);
-  constexpr int NA = FUSE_GRAM ? NT : 1;
-  A acc[NA][NB];
+  A acc[NT][NB];
 #pragma unroll
-  for (int t = 0; t < NA; ++t)
+  for (int t = 0; t < NT; ++t)
 #pragma unroll
     for (int b = 0; b < NB; ++b) acc[t][b] = Pol::zero();
   for (int r = r0 + warp; r < r1; r += kWarps) {
-    A d[NB];
-    if constexpr (!FUSE_GRAM) {
-      // the update by the second pass's coefficients: products of the heads in FP32
-      T qr[NT];
+    // Q[r, :] c, two interleaved accumulators per new vector (independent chains)
+    A d[NB], d1[NB];
 #pragma unroll
-      for (int t = 0; t < NT; ++t) {
-        const int i = lane + 32 * t;
-        qr[t] = i < ncols ? __ldg(Q + (long long)r * J.ldq + i) : T{};
+    for (int b = 0; b < NB; ++b) d[b] = d1[b] = Pol::zero();
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      const int i = lane + 32 * t;
+      if (i < ncols) {
+        const Sp qs = Pol::split(__ldg(Q + (long long)r * J.ldq + i));
+#pragma unroll
+        for (int b = 0; b < NB; ++b) Pol::mac_s((t & 1) ? d1[b] : d[b], qs, cs[b * ncols + i]);
       }
-      typename Pol::F f[NB];
+    }
 #pragma unroll
-      for (int b = 0; b < NB; ++b) f[b] = Pol::fzero();
+    for (int b = 0; b < NB; ++b) {
+      d[b] = Pol::add(d[b], d1[b]);
 #pragma unroll
-      for (int t = 0; t < NT; ++t) {
-        const int i = lane + 32 * t;
-        if (i < ncols)
-#pragma unroll
-          for (int b = 0; b < NB; ++b) Pol::fmac(f[b], qr[t], cs[b * ncols + i]);
-      }
-#pragma unroll
-      for (int b = 0; b < NB; ++b) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) f[b] = Pol::fadd(f[b], Pol::fshfl_xor(f[b], o));
-        d[b] = Pol::fto_A(f[b]);
-      }
-    } else {
-      // the row's basis values are read again (from L1) for the Gram below
-      // rather than held in registers: half the registers, twice the warps
-      // two interleaved accumulators per new vector: independent chains
-      A d1[NB];
-#pragma unroll
-      for (int b = 0; b < NB; ++b) d[b] = d1[b] = Pol::zero();
-#pragma unroll
-      for (int t = 0; t < NT; ++t) {
-        const int i = lane + 32 * t;
-        if (i < ncols) {
-          const Sp qs = Pol::split(__ldg(Q + (long long)r * J.ldq + i));
-#pragma unroll
-          for (int b = 0; b < NB; ++b) Pol::mac_s((t & 1) ? d1[b] : d[b], qs, cs[b * ncols + i]);
-        }
-      }
-#pragma unroll
-      for (int b = 0; b < NB; ++b) d[b] = Pol::add(d[b], d1[b]);
-#pragma unroll
-      for (int b = 0; b < NB; ++b)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) d[b] = Pol::add(d[b], Pol::shfl_xor(d[b], o));
+      for (int o = 16; o > 0; o >>= 1) d[b] = Pol::add(d[b], Pol::shfl_xor(d[b], o));
     }
     // the row's new values are formed by lane 0 alone (FP32 instructions
     // only, in split form) and broadcast
@@ -385,28 +351,25 @@ __global__ void __launch_bounds__(kThreads, (NT <= 8) ? 2 : 1) sv_update_kernel(
         w[(long long)r * J.ldw + b] = Pol::wstore(ws[b]);
       }
     }
-    if (FUSE_GRAM) {
 #pragma unroll
-      for (int b = 0; b < NB; ++b) ws[b] = Pol::bcast0(ws[b]);
+    for (int b = 0; b < NB; ++b) ws[b] = Pol::bcast0(ws[b]);
 #pragma unroll
-      for (int t = 0; t < NT; ++t) {
-        const int i = lane + 32 * t;
-        if (i < ncols) {
-          const Sp qs = Pol::split(__ldg(Q + (long long)r * J.ldq + i));
+    for (int t = 0; t < NT; ++t) {
+      const int i = lane + 32 * t;
+      if (i < ncols) {
+        const Sp qs = Pol::split(__ldg(Q + (long long)r * J.ldq + i));
 #pragma unroll
-          for (int b = 0; b < NB; ++b) Pol::conj_mac_s(acc[FUSE_GRAM ? t : 0][b], qs, ws[b]);
-        }
+        for (int b = 0; b < NB; ++b) Pol::conj_mac_s(acc[t][b], qs, ws[b]);
       }
     }
   }
   double2* out = J.part + (long long)blockIdx.x * J.ldp;
-  if (!FUSE_GRAM) return;
   // cross-warp sums, one 32-column slab at a time: red [kWarps][NB][32]
 #pragma unroll
   for (int t = 0; t < NT; ++t) {
     if (32 * t >= ncols) break;  // uniform over the block
 #pragma unroll
-    for (int b = 0; b < NB; ++b) red[(warp * NB + b) * 32 + lane] = Pol::to_d(acc[FUSE_GRAM ? t : 0][b]);
+    for (int b = 0; b < NB; ++b) red[(warp * NB + b) * 32 + lane] = Pol::to_d(acc[t][b]);
     __syncthreads();
     if (threadIdx.x < 32 * NB) {
       const int b = threadIdx.x >> 5, l = threadIdx.x & 31, i = l + 32 * t;
@@ -679,13 +642,13 @@ void launch_update_nt(const SvBatch& b, int N, int rpc, int maxcols, cudaStream_
       SWI_CUDA_TRY(cudaFuncSetAttribute(sv_update_fast_kernel<Pol, NT, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)smem));
     sv_update_fast_kernel<Pol, NT, NB><<<dim3(nchunks, b.n), kThreads, smem, s>>>(b, N, rpc);
-    return;
+  } else {
+    const size_t smem = sizeof(double2) * ((size_t)maxcols * NB + (size_t)kWarps * NB * 32);
+    if (smem > 48 * 1024)
+      SWI_CUDA_TRY(cudaFuncSetAttribute(sv_update_kernel<Pol, NT, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem));
+    sv_update_kernel<Pol, NT, NB><<<dim3(nchunks, b.n), kThreads, smem, s>>>(b, N, rpc);
   }
-  const size_t smem = sizeof(double2) * ((size_t)maxcols * NB + (FUSE ? (size_t)kWarps * NB * 32 : kWarps * NB * NB));
-  if (smem > 48 * 1024)
-    SWI_CUDA_TRY(cudaFuncSetAttribute(sv_update_kernel<Pol, NT, NB, FUSE>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  sv_update_kernel<Pol, NT, NB, FUSE><<<dim3(nchunks, b.n), kThreads, smem, s>>>(b, N, rpc);
 }
 
 template <class Pol, int NB, bool FUSE>

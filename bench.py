@@ -621,7 +621,7 @@ def main():
                    "matvec_budget_per_window": budget,
                    "sigma": [round(float(x), 5) for x in sig], "n_req": [int(x) for x in req],
                    "per_window": [{"n_conv": x["n_conv"], "matvecs": x["matvecs"], "restarts": x["restarts"],
-                                   "basis": x["basis"]} for x in winfo],
+                                   "basis": x["basis"], "schur_retries": x["schur_retries"]} for x in winfo],
                    "arith": "complex128 Krylov basis; classical Gram-Schmidt twice as three passes over each basis: "
                             "Gram in FP32, update plus second Gram in double-single (2 x FP32), second update (by "
                             "the small second-pass coefficients) in FP32 with the new vector kept in double-single; "
@@ -652,7 +652,7 @@ def main():
         log("single window")
         try:
             lam = ks_spectrum(WORKLOAD)
-            out["single_window"] = single_window(swi, stream, wire, lam, n_r, 4000)
+            out["single_window"] = single_window(swi, stream, wire, lam, n_r, 9000)
         except (RuntimeError, OSError) as e:
             out["single_window"] = {"error": str(e)}
         log("residual-correction sweep")

@@ -121,6 +121,9 @@ typedef struct {
   int restarts;
   int basis;            /* m_j used */
   double max_res;       /* largest relative residual of the delivered pairs */
+  int schur_retries;    /* restarts whose double-single Schur step gave up and
+                           were recomputed in native FP64 */
+  int reserved;
 } swi_window_info;
 
 typedef struct {

@@ -76,7 +76,8 @@ class PlanInfo(C.Structure):
 
 class WindowInfo(C.Structure):
     _fields_ = [("sigma", C.c_double), ("n_req", C.c_int), ("n_conv", C.c_int), ("matvecs", C.c_longlong),
-                ("restarts", C.c_int), ("basis", C.c_int), ("max_res", C.c_double)]
+                ("restarts", C.c_int), ("basis", C.c_int), ("max_res", C.c_double), ("schur_retries", C.c_int),
+                ("reserved", C.c_int)]
 
 
 class SolveInfo(C.Structure):

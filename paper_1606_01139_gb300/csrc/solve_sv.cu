@@ -555,6 +555,7 @@ swi_status solve_sv(swi_ctx* c, const swi_solve_opts& opt, swi_solve_info* info)
     double mr = 0.0;
     for (double r : rw) mr = std::max(mr, r / anorm);
     wi.max_res = mr;
+    wi.schur_retries = w.schur_retries;
     double2 flag;
     SWI_CUDA_TRY(cudaMemcpy(&flag, w.rinv.template as<double2>() + 8, sizeof(double2), cudaMemcpyDeviceToHost));
     if (flag.x != 0.0) any_breakdown = true;

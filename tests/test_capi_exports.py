@@ -71,3 +71,34 @@ def test_null_context_is_rejected_by_every_entry_taking_one(lib):
     assert L.swi_refine(None, None, None) == swi.SWI_EINVAL
     assert L.swi_residuals(None, None) == swi.SWI_EINVAL
     assert L.swi_transmission(None, 1, None, None) == swi.SWI_EINVAL
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    # the ctypes structures of the binding have the C layout of include/swi.h:
+    # size and the offset of every field, compiled with the host C compiler
+    import shutil
+    import subprocess
+    import paper_1606_01139_gb300 as swi
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    pairs = [("swi_solve_opts", swi.SolveOpts), ("swi_solve_info", swi.SolveInfo),
+             ("swi_window_info", swi.WindowInfo), ("swi_refine_opts", swi.RefineOpts),
+             ("swi_refine_info", swi.RefineInfo), ("swi_plan_opts", swi.PlanOpts), ("swi_plan_info", swi.PlanInfo),
+             ("swi_kernel_stats", swi.KernelStats)]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "swi.h"', "int main(void) {"]
+    for cname, py in pairs:
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f in py._fields_:
+            lines.append(f'  printf("{cname} {f[0]} %zu\\n", offsetof({cname}, {f[0]}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in pairs:
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f in py._fields_:
+            assert got[(cname, f[0])] == getattr(py, f[0]).offset, (cname, f[0])

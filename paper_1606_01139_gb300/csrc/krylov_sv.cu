@@ -6,13 +6,18 @@
 //
 // Every window keeps its basis row-major, Q [N][ld] (a grid point's basis
 // coefficients are contiguous), so each pass of classical Gram-Schmidt against
-// the single new vector w streams the basis once (HBM-bound).  Two element
-// types share the kernels through an arithmetic policy:
+// the new vectors w streams the basis once.  Classical Gram-Schmidt twice is
+// three passes: the Gram (FP32 products of the heads), the update fused with
+// the second Gram (the accurate pass), and the update by the second pass's
+// small coefficients (FP32 products).  Two element types share the kernels
+// through an arithmetic policy:
 //  - complex64 with FP32 arithmetic (the reduced-precision form);
 //  - complex128 in double-single arithmetic: every FP64 operand split into a
 //    float head and tail from its bit fields, products exact up to their
 //    tails (FMA), sums TwoSum-compensated, ~2^-46 relative per term (GB300's
-//    FP64 rate would cap these passes near a third of the HBM bandwidth).
+//    FP64 rate would cap these passes near a third of the HBM bandwidth); the
+//    new vectors themselves are kept in split form while they are
+//    orthogonalised.
 //
 //  sv_gram_kernel:   part[chunk][i][b] = sum_{rows of chunk} conj(Q[r, i]) w[r, b]
 //                    (a block per 32-column slab and row chunk, one column per lane)
@@ -633,6 +638,7 @@ __global__ void sv_normalize_kernel(const __grid_constant__ SvNormBatch batch, i
   }
 }
 
+// FUSE: the accurate pass (update + second Gram), else the FP32 second update
 template <class Pol, int NT, int NB, bool FUSE>
 void launch_update_nt(const SvBatch& b, int N, int rpc, int maxcols, cudaStream_t s) {
   const int nchunks = (N + rpc - 1) / rpc;

@@ -69,6 +69,56 @@ def hole_window(eps_lower_window, eps_upper_window, e_min: float, e_max: float, 
     return shift, n_req
 
 
+def hole_window_local(eps_lower_window, eps_upper_window, e_min: float, e_max: float, N: int, cap: int = 300):
+    """Hole window with the request taken from the local spacing (a reading).
+
+    Algorithm 1 sizes the request from the uniform spacing (E_max - E_min)/N;
+    Section 2.2.1 suggests sampling the local density instead.  Reading: the
+    mean spacing of the real parts the two neighbouring windows delivered
+    (when they hold at least 4), 3/2 of the gap's count at that spacing plus 4
+    (the new window must reach past both edges of the gap to overlap its
+    neighbours), at most ``cap``; with fewer than 4 values, Algorithm 1's
+    request (``hole_window``).  The shift is the same: the middle of the gap.
+    """
+    lo_re = np.real(np.asarray(eps_lower_window))
+    hi_re = np.real(np.asarray(eps_upper_window))
+    top, bot = float(np.max(lo_re)), float(np.min(hi_re))
+    shift = 0.5 * (top + bot)
+    both = np.concatenate([lo_re, hi_re])
+    if len(both) >= 4 and both.max() > both.min():
+        spacing = (both.max() - both.min()) / (len(both) - 1)
+        n_req = math.ceil(1.5 * (bot - top) / spacing) + 4
+    else:
+        n_req = math.ceil(1.5 * (bot - top) / ((e_max - e_min) / N))
+    return shift, int(min(cap, max(1, n_req)))
+
+
+def merge_samples(spectrum, sample, prev_top: float, tol: float):
+    """Add a sampling window's real parts to the sampled spectrum, with multiplicity (a reading).
+
+    Section 2.2.1: a few eigenpairs at sample points estimate the density.
+    Consecutive sample windows overlap, so a value found twice must count
+    once; a twofold eigenvalue found twice in one sample must count twice.
+    Values within tau = max(1e-7, 100 tol) max(1, |x|) of each other are one
+    value up to multiplicity: a value of the sample is added when its rank
+    among the sample's copies exceeds the copies already in the spectrum;
+    values below prev_top - tau are already covered.
+    """
+    have = list(spectrum)
+    out = list(spectrum)
+    r = sorted(float(x) for x in sample)
+    tau_rel = max(1e-7, 100.0 * tol)
+    for i, x in enumerate(r):
+        tau = tau_rel * max(1.0, abs(x))
+        if x < prev_top - tau:
+            continue
+        rank = sum(1 for k in range(i + 1) if abs(r[k] - x) <= tau)
+        old = sum(1 for y in have if abs(y - x) <= tau)
+        if rank > old:
+            out.append(x)
+    return out
+
+
 def combine(eps_list, U_list, eq_rtol: float = 1e-8, drop_tol: float = 1e-6):
     """Algorithm 2 over windows given in shift order.
 

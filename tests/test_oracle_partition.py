@@ -57,6 +57,39 @@ def _bilinear_unit(v):
     return v / np.sqrt(v @ v)
 
 
+def test_hole_window_local_by_hand():
+    # lower window real parts 0.0, 0.1, 0.2, 0.3; upper 0.9, 1.0: 6 values over
+    # [0, 1], mean spacing 1/5 = 0.2; gap 0.3 .. 0.9 = 0.6, 3/2 x 0.6/0.2 = 4.5
+    # -> 5, plus 4 = 9; shift at 0.6
+    s, n = partition.hole_window_local([0.0, 0.1, 0.2 - 0.01j, 0.3], [0.9, 1.0], 0.0, 2.0, 64)
+    assert abs(s - 0.6) < 1e-15 and n == 9
+    # fewer than 4 values: Algorithm 1's uniform request (as hole_window)
+    assert partition.hole_window_local([0.25, 1.0], [1.5], 0.0, 2.0, 64) == \
+        partition.hole_window([0.25, 1.0], [1.5], 0.0, 2.0, 64)
+    # the cap
+    _, n = partition.hole_window_local([0.0, 0.1, 0.2, 0.3], [0.9, 1.0], 0.0, 2.0, 64, cap=5)
+    assert n == 5
+
+
+def test_merge_samples_counts_with_multiplicity():
+    tol = 1e-8  # tau = 1e-6 max(1, |x|)
+    spec = [0.1, 0.2, 0.3]
+    # a repeat of values already sampled (overlapping windows) counts once;
+    # values below the previous top are covered; a new value is added
+    out = partition.merge_samples(spec, [0.2 + 1e-9, 0.3 - 1e-9, 0.4], prev_top=0.3, tol=tol)
+    assert out == [0.1, 0.2, 0.3, 0.4]
+    # a twofold value at the previous top: the earlier sample held one copy,
+    # this one holds both -> one more copy
+    out = partition.merge_samples(spec, [0.3, 0.3 + 2e-9, 0.5], prev_top=0.3, tol=tol)
+    assert sorted(out) == [0.1, 0.2, 0.3, 0.3 + 2e-9, 0.5]
+    # a new twofold value above counts twice
+    out = partition.merge_samples(spec, [0.6, 0.6], prev_top=0.3, tol=tol)
+    assert out == [0.1, 0.2, 0.3, 0.6, 0.6]
+    # distinct values farther apart than tau are separate
+    out = partition.merge_samples([], [1.0, 1.0 + 1e-5], prev_top=-np.inf, tol=tol)
+    assert out == [1.0, 1.0 + 1e-5]
+
+
 def test_combine_removes_duplicates_and_keeps_degenerate_partners():
     rng = np.random.default_rng(0)
     N = 50

@@ -66,7 +66,7 @@ enum { SWI_ARITH_DS = 2, SWI_ARITH_F64 = 1 };     /* see swi_solve_opts.arith */
 /* Options of swi_solve.  Zero-initialise and set what you need; zero fields
  * take the defaults given here. */
 typedef struct {
-  int block;            /* b, Krylov block width (default 16; 1..32).  b = 1
+  int block;            /* b, Krylov block width (default 2; 1..32).  b = 1
                            selects single-vector windows, the form of the
                            paper's implicitly restarted Arnoldi: every window
                            adds one vector per step, all windows share each
@@ -77,9 +77,12 @@ typedef struct {
                            inside the pair): one starting vector spans only one
                            vector of each eigenspace, so eigenvalues of
                            multiplicity two (a symmetric cross-section) need
-                           b = 2 for both partners.  SWI_PREC_MIXED contexts
-                           run these forms only (b = 0 or 1: one vector, 2: two),
-                           on complex64 bases with FP32 arithmetic */
+                           b = 2 for both partners.  b >= 3 runs wide blocks
+                           (block Gram-Schmidt on tensor-core digit products;
+                           SWI_ARITH_F64 always runs that form, b = 0 there
+                           meaning 16).  SWI_PREC_MIXED contexts run the 1- and
+                           2-vector forms only, on complex64 bases with FP32
+                           arithmetic */
   int max_basis;        /* m_j, basis size before a restart (default
                            max(2 n_req + 1, keep + (8 + j mod 3) b) rounded
                            up to b, j the window index: the stagger keeps
@@ -93,9 +96,12 @@ typedef struct {
   int arith;            /* arithmetic of the Krylov loop and T(E):
                            0 or SWI_ARITH_DS (default) -- stencil, Cholesky-QR,
                            projected Schur step and T(E) projections in
-                           double-single on the FP32 pipes, Gram-Schmidt
-                           products and restart rotation on the tensor cores
-                           with an exact digit split, ~1e-13 relative;
+                           double-single on the FP32 pipes; for b <= 2 the
+                           Gram-Schmidt passes as described with the kernels
+                           (FP32 first Gram and second update, double-single
+                           accurate pass), for b >= 3 Gram-Schmidt products and
+                           the restart rotation on the tensor cores with an
+                           exact digit split; ~1e-13 relative;
                            SWI_ARITH_F64 -- native FP64 throughout.  The final
                            explicit residual check is native FP64 in both. */
   long long max_matvecs;/* per-window budget of operator applications per

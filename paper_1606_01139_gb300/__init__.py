@@ -285,7 +285,7 @@ class Context:
         return Y
 
     # -- solve
-    def solve(self, block=16, rel_tol=1e-10, max_basis=0, keep=0, max_matvecs=0, eq_rtol=0.0, drop_tol=0.0,
+    def solve(self, block=2, rel_tol=1e-10, max_basis=0, keep=0, max_matvecs=0, eq_rtol=0.0, drop_tol=0.0,
               seed=1, n_keep=0, arith=ARITH_DS, allow=(SWI_OK, SWI_ENOCONV, SWI_HOLES)):
         """Windowed solve; arith = ARITH_DS (double-single products, default) or ARITH_F64 (native).
 
@@ -301,7 +301,7 @@ class Context:
         d["status"] = STATUS_NAMES[rc]
         return d
 
-    def solve_more(self, sigma, n_req, block=16, rel_tol=1e-10, max_basis=0, keep=0, max_matvecs=0, eq_rtol=0.0,
+    def solve_more(self, sigma, n_req, block=2, rel_tol=1e-10, max_basis=0, keep=0, max_matvecs=0, eq_rtol=0.0,
                    drop_tol=0.0, seed=1, n_keep=0, arith=ARITH_DS, allow=(SWI_OK, SWI_ENOCONV, SWI_HOLES)):
         """Continuation: solve new windows and merge them with the current pairs (Algorithm 2)."""
         s, n = _c_arr(sigma, np.float64), _c_arr(n_req, np.int32)
@@ -313,7 +313,7 @@ class Context:
         d["status"] = STATUS_NAMES[rc]
         return d
 
-    def fill_holes(self, e_min, e_max, max_rounds=0, block=16, rel_tol=1e-10, max_basis=0, keep=0, max_matvecs=0,
+    def fill_holes(self, e_min, e_max, max_rounds=0, block=2, rel_tol=1e-10, max_basis=0, keep=0, max_matvecs=0,
                    eq_rtol=0.0, drop_tol=0.0, seed=1, n_keep=0, arith=ARITH_DS,
                    allow=(SWI_OK, SWI_ENOCONV, SWI_HOLES)):
         """Algorithm 1's hole loop on the current windows; returns the info dict with "status", "windows_added"."""

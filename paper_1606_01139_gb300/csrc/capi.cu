@@ -1254,16 +1254,21 @@ swi_status swi_apply_c64(swi_ctx* c, int nvec, const float* sigma, const void* X
   });
 }
 
-// the solver of the context's precision and the options' block width
+// the solver of the context's precision and the options' block width (block
+// 0 selects the batched windows of 2-vector blocks; with native FP64, wide
+// blocks of 16)
 static swi_status solve_dispatch(swi_ctx* c, const swi_solve_opts* opts, swi_solve_info* info) {
+  swi_solve_opts o;
+  std::memset(&o, 0, sizeof(o));
+  if (opts) o = *opts;
+  if (o.block == 0) o.block = (o.arith == SWI_ARITH_F64 && c->precision != SWI_PREC_MIXED) ? 16 : 2;
   if (c->precision == SWI_PREC_MIXED) {
-    if (opts && opts->block > 2)
-      return fail(c, SWI_EINVAL, "SWI_PREC_MIXED runs windows of 1 or 2 vectors (block 0, 1 or 2)");
-    if (opts && opts->arith == SWI_ARITH_F64) return fail(c, SWI_EINVAL, "SWI_PREC_MIXED has no native-FP64 form");
-    return do_solve_sv(c, opts, info);
+    if (o.block > 2) return fail(c, SWI_EINVAL, "SWI_PREC_MIXED runs windows of 1 or 2 vectors (block 0, 1 or 2)");
+    if (o.arith == SWI_ARITH_F64) return fail(c, SWI_EINVAL, "SWI_PREC_MIXED has no native-FP64 form");
+    return do_solve_sv(c, &o, info);
   }
-  if (opts && (opts->block == 1 || opts->block == 2) && opts->arith != SWI_ARITH_F64) return do_solve_sv(c, opts, info);
-  return do_solve(c, opts, info);
+  if (o.block <= 2 && o.arith != SWI_ARITH_F64) return do_solve_sv(c, &o, info);
+  return do_solve(c, &o, info);
 }
 
 swi_status swi_solve(swi_ctx* c, const swi_solve_opts* opts, swi_solve_info* info) {

@@ -30,6 +30,7 @@ constexpr int kMaxOwners = 384;
 // matrices of order 240-384 (deflations inside the active window) exhausted
 // the QR iteration limit in that path, so larger orders take the plain sweep.
 constexpr int kOwnerPathMaxM = 224;
+static_assert(kOwnerPathMaxM <= kMaxOwners, "every row and column of the sweep needs an owner thread");
 __device__ __forceinline__ int owner_index(int tid) {
   const int w = tid >> 5;
   if ((w & 3) == 0) return -1;

@@ -96,18 +96,6 @@ __device__ __forceinline__ void rot_cols(dc& a1, dc& a2, const RotD& g) {
   a2 = csub(cscale(b, g.c), cmul(g.s, a));
 }
 
-__device__ float block_reduce_sumf(float v, float* red) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  __syncthreads();
-  if (l == 0) red[w] = v;
-  __syncthreads();
-  float s = 0.f;
-  for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[q];
-  __syncthreads();
-  return s;
-}
-
 // double-single reduction (sum of df over the block)
 __device__ df block_reduce_df(df v, df* red) {
   for (int o = 16; o > 0; o >>= 1) {

@@ -384,6 +384,29 @@ swi_status swi_refine(swi_ctx* ctx, const swi_refine_opts* opts, swi_refine_info
  * Errors: SWI_ESTATE (no pairs), SWI_EINVAL. */
 swi_status swi_transmission(swi_ctx* ctx, int nE, const double* E, double* T_out);
 
+/* Arithmetic of the T(E) and adjoint contractions of swi_transmission and
+ * swi_grad (Section 1's T = Tr{G Gamma_R G^dagger Gamma_L} through the
+ * spectral G).  SWI_CONTRACT_F64 (the default): FP64-class products.
+ * SWI_CONTRACT_F32: FP32 products with FP32 accumulation:
+ *  - the projections U^H Gamma U take U rounded to complex64 and run over the
+ *    rows where the absorber, rounded to FP32, is a normal number (the other
+ *    rows contribute exact zeros in FP32, or less than 2^-126 |U_ra||U_rc|);
+ *    each thread adds 256-row block sums, and the row chunks' partial sums are
+ *    added in FP64;
+ *  - W = R o L, T_e and dT_e/dE_e are then formed in FP64 (n_E n^2 work);
+ *  - the adjoint M = sum_e w_e D_e R conj(D_e) L^T D_e and
+ *    dL/dV(r) = 2 Re sum_ac U_ra M_ac U_rc run in FP32 (U M is never stored:
+ *    no N x n scratch), with |E_e - eps_k| above ~1e-38 so that g fits FP32.
+ * The results carry FP32 rounding: relative to the sums of the magnitudes of
+ * their terms, errors of order (accumulation length) x 2^-24.
+ * swi_transmission_noalloc always uses the FP64-class products.  Changing the
+ * setting drops the cached projections.  Errors: SWI_EINVAL (another value). */
+enum {
+  SWI_CONTRACT_F64 = 0,
+  SWI_CONTRACT_F32 = 1
+};
+swi_status swi_set_contraction(swi_ctx* ctx, int contraction);
+
 /* Vector-Jacobian product of T (the adjoint of the spectral T(E) of Section 1,
  * with dG = G dV G): given dL/dT_e (nE host doubles), writes
  *   dL/dV(r) = sum_e dLdT_e 2 Re[(G Gamma_R G^dagger Gamma_L G)_rr]

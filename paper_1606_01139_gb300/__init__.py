@@ -23,12 +23,13 @@ STATUS_NAMES = {0: "SWI_OK", 1: "SWI_EINVAL", 2: "SWI_ENOMEM", 3: "SWI_ECUDA", 4
 BC_ODD, BC_ZERO = 0, 1
 PREC_F64, PREC_MIXED = 0, 1
 ARITH_DS, ARITH_F64 = 2, 1
+CONTRACT_F64, CONTRACT_F32 = 0, 1
 
 # Every entry point declared in include/swi.h.
 EXPORTS = ("swi_create", "swi_set_potential", "swi_set_absorber", "swi_set_windows", "swi_plan_windows", "swi_plan_windows_sampled",
            "swi_apply", "swi_apply_ds", "swi_apply_c64", "swi_solve", "swi_solve_more", "swi_fill_holes",
            "swi_get_windows", "swi_refine", "swi_get_window_info", "swi_get_eigenpairs", "swi_copy_eigenpairs",
-           "swi_set_eigenpairs", "swi_residuals", "swi_transmission", "swi_grad", "swi_profile",
+           "swi_set_eigenpairs", "swi_residuals", "swi_transmission", "swi_set_contraction", "swi_grad", "swi_profile",
            "swi_profile_read", "swi_transmission_noalloc", "swi_check_schur", "swi_last_error", "swi_launch_count",
            "swi_destroy")
 
@@ -123,6 +124,7 @@ def load(path: str = LIB_PATH):
         "swi_set_eigenpairs": (I, [VP, I, VP, VP, I]),
         "swi_residuals": (I, [VP, VP]),
         "swi_transmission": (I, [VP, I, VP, VP]),
+        "swi_set_contraction": (I, [VP, I]),
         "swi_grad": (I, [VP, I, VP, VP, VP, I, VP]),
         "swi_profile": (I, [VP, I]),
         "swi_transmission_noalloc": (I, [VP, I, VP, VP]),
@@ -392,6 +394,11 @@ class Context:
         T = np.empty_like(E)
         self._check(self._lib.swi_transmission(self._h, len(E), _ptr(E), _ptr(T)))
         return T
+
+    def set_contraction(self, contraction):
+        """Arithmetic of transmission() and grad(): CONTRACT_F64 (default) or CONTRACT_F32
+        (FP32 products with FP32 accumulation for the projections and the adjoint)."""
+        return self._check(self._lib.swi_set_contraction(self._h, int(contraction)))
 
     def transmission_noalloc(self, E):
         """T(E) through swi_transmission_noalloc: no device allocation during the call.

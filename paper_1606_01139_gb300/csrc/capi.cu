@@ -8,6 +8,7 @@
 // batched launches, and windows that reach their maximum basis restart
 // together.  The host reads back only a few status words per restart.
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 #include <cstring>
 #include <memory>
@@ -962,6 +963,20 @@ void ensure_RL(swi_ctx* c) {
   c->Rm.ensure(sizeof(double2) * nn);
   c->Lm.ensure(sizeof(double2) * nn);
   c->Wm.ensure(sizeof(double2) * nn);
+  if (c->contract == SWI_CONTRACT_F32) {
+    const long long rR = c->gR_hi - c->gR_lo, rL = c->gL_hi - c->gL_lo;
+    const int kR = swi::proj_f32_chunks(n, rR), kL = swi::proj_f32_chunks(n, rL);
+    c->R32.ensure(sizeof(float2) * nn);
+    c->L32.ensure(sizeof(float2) * nn);
+    c->part32.ensure(sizeof(float2) * nn * (size_t)std::max(kR + kL, 1));
+    const double2* U = c->U.as<double2>();
+    ProfScope ps(c, SWI_K_PROJ, 8.0 * (double)(rR + rL) * n * n, 16.0 * (double)(rR + rL) * n + 8.0 * (rR + rL));
+    swi::launch_proj_f32(U, n, n, c->gR.as<double>(), c->gR_lo, c->gR_hi, c->gL.as<double>(), c->gL_lo, c->gL_hi,
+                         c->part32.as<float2>(), c->Rm.as<double2>(), c->Lm.as<double2>(), c->Wm.as<double2>(),
+                         c->R32.as<float2>(), c->L32.as<float2>(), c->stream, &c->launches);
+    c->have_RL = true;
+    return;
+  }
   gram_work_ensure(c, nn * 4);
   ProfScope ps(c, SWI_K_PROJ, 2.0 * 8.0 * c->N * (double)n * n, 2.0 * 16.0 * c->N * (double)n + 16.0 * c->N);
   swi::GramBatch gb;
@@ -1109,11 +1124,19 @@ swi_status swi_set_absorber(swi_ctx* c, const double* gL, const double* gR, int 
       std::memcpy(r.data(), gR, sizeof(double) * n);
     }
     double mx = 0.0;
+    long long lo[2] = {-1, -1}, hi[2] = {0, 0};
     for (size_t i = 0; i < n; ++i) {
       if (!std::isfinite(l[i]) || !std::isfinite(r[i]) || l[i] < 0.0 || r[i] < 0.0)
         return fail(c, SWI_EINVAL, "absorbers must be finite and non-negative");
       g[i] = l[i] + r[i];
       mx = std::max(mx, g[i]);
+      // rows whose FP32 absorber is a normal number (those of the FP32 projections)
+      const double v[2] = {l[i], r[i]};
+      for (int k = 0; k < 2; ++k)
+        if ((float)v[k] >= FLT_MIN) {
+          if (lo[k] < 0) lo[k] = (long long)i;
+          hi[k] = (long long)i + 1;
+        }
     }
     copy_in(c->gL, l.data(), sizeof(double) * n, false, c->stream);
     copy_in(c->gR, r.data(), sizeof(double) * n, false, c->stream);
@@ -1125,6 +1148,10 @@ swi_status swi_set_absorber(swi_ctx* c, const double* gL, const double* gR, int 
     }
     sync(c->stream);
     c->maxG = mx;
+    c->gL_lo = lo[0] < 0 ? 0 : lo[0];
+    c->gL_hi = lo[0] < 0 ? 0 : hi[0];
+    c->gR_lo = lo[1] < 0 ? 0 : lo[1];
+    c->gR_hi = lo[1] < 0 ? 0 : hi[1];
     c->has_G = true;
     c->have_RL = false;
     refresh_vg(c);
@@ -1395,6 +1422,16 @@ swi_status swi_transmission(swi_ctx* c, int nE, const double* E, double* T_out) 
   });
 }
 
+swi_status swi_set_contraction(swi_ctx* c, int contraction) {
+  return guarded(c, [&]() -> swi_status {
+    if (contraction != SWI_CONTRACT_F64 && contraction != SWI_CONTRACT_F32)
+      return fail(c, SWI_EINVAL, "contraction must be SWI_CONTRACT_F64 or SWI_CONTRACT_F32");
+    if (contraction != c->contract) c->have_RL = false;
+    c->contract = contraction;
+    return SWI_OK;
+  });
+}
+
 swi_status swi_grad(swi_ctx* c, int nE, const double* E, const double* dLdT, double* dLdV, int dLdV_on_device,
                     double* dLdE) {
   return guarded(c, [&]() -> swi_status {
@@ -1414,7 +1451,27 @@ swi_status swi_grad(swi_ctx* c, int nE, const double* E, const double* dLdT, dou
                                c->Tbuf.as<double>(), c->dEbuf.as<double>(), c->stream, &c->launches);
       SWI_CUDA_TRY(cudaMemcpyAsync(dLdE, c->dEbuf.p, sizeof(double) * nE, cudaMemcpyDeviceToHost, c->stream));
     }
-    if (dLdV) {
+    if (dLdV && c->contract == SWI_CONTRACT_F32) {
+      copy_in(c->wbuf, dLdT, sizeof(double) * nE, false, c->stream);
+      c->gt32.ensure(sizeof(float2) * (size_t)nE * n);
+      c->M32.ensure(sizeof(float2) * (size_t)n * n);
+      DevMem tmp;
+      double* dst = dLdV;
+      if (!dLdV_on_device) {
+        tmp.ensure(sizeof(double) * c->N);
+        dst = tmp.as<double>();
+      }
+      {
+        ProfScope ps(c, SWI_K_GRAD, 8.0 * (double)n * n * ((double)nE * n + c->N),
+                     16.0 * c->N * (double)n + 8.0 * c->N);
+        swi::launch_grad_f32(c->R32.as<float2>(), c->L32.as<float2>(), c->eps.as<double2>(), n, c->Ebuf.as<double>(),
+                             c->wbuf.as<double>(), nE, c->gt32.as<float2>(), c->M32.as<float2>(), c->U.as<double2>(),
+                             n, (long long)c->N, dst, c->stream, &c->launches);
+      }
+      if (!dLdV_on_device)
+        SWI_CUDA_TRY(cudaMemcpyAsync(dLdV, dst, sizeof(double) * c->N, cudaMemcpyDeviceToHost, c->stream));
+      sync(c->stream);
+    } else if (dLdV) {
       copy_in(c->wbuf, dLdT, sizeof(double) * nE, false, c->stream);
       c->Mg.ensure(sizeof(double2) * (size_t)n * n);
       ProfScope ps(c, SWI_K_GRAD, 8.0 * (double)n * n * ((double)nE * n + c->N),

@@ -94,9 +94,14 @@ struct swi_ctx {
   DevMem eps, U;  // [n], [N][n]
   std::vector<double> resid;
   std::vector<swi_window_info> winfo;
+  // rows of each absorber whose FP32 value is a normal number ([lo, hi), empty
+  // when there is none): the row range of the FP32 projections
+  long long gL_lo = 0, gL_hi = 0, gR_lo = 0, gR_hi = 0;
   // transport cache
+  int contract = SWI_CONTRACT_F64;
   bool have_RL = false;
   DevMem MR, ML, Rm, Lm, Wm, Mg, Ebuf, Tbuf, dEbuf, wbuf;
+  DevMem R32, L32, part32, gt32, M32;  // FP32 contractions
   // workspaces
   DevMem gram_work, sig_dev, colwork, scratch, Uall, ordinfo, cholstat, ptrs, dres;
   // merge scratch

@@ -184,6 +184,24 @@ swi_status swi_set_absorber(swi_ctx* ctx, const double* gamma_L, const double* g
  * n_req[j] >= 1 (host arrays).  Errors: SWI_EINVAL. */
 swi_status swi_set_windows(swi_ctx* ctx, int p, const double* sigma, const int* n_req);
 
+/* Windows with complex shifts sigma_j = sigma_re[j] + i sigma_im[j]: the
+ * two-dimensional partition Section 2 names for strongly non-Hermitian
+ * problems, whose eigenvalues lie further below the real axis.  Window j
+ * delivers the n_req[j] eigenpairs whose eigenvalues are nearest sigma_j (the
+ * SM rule on A - sigma_j).  The operator applied is A - sigma_re[j]: the Krylov
+ * space does not depend on the shift, and the imaginary part enters only the
+ * selection, which ranks the Ritz values theta of A - sigma_re[j] by
+ * |theta - i sigma_im[j]|.  Shifts strictly increasing by (Re, Im); host
+ * arrays.  Solved by windows of 1 or 2 vectors (swi_solve with block 0, 1 or
+ * 2 and the double-single or mixed arithmetic; SWI_EINVAL otherwise).  The
+ * merged pairs are all kept when swi_solve_opts.n_keep is 0; the merge's
+ * interface flags refer to consecutive windows in the order given, and
+ * swi_fill_holes refuses such a solve (SWI_EINVAL).  swi_set_windows and the
+ * planners set real shifts again; swi_get_windows reports the real parts.
+ * Errors: SWI_EINVAL. */
+swi_status swi_set_windows_complex(swi_ctx* ctx, int p, const double* sigma_re, const double* sigma_im,
+                                   const int* n_req);
+
 /* Plan p windows for the lowest n_r pairs with Algorithm 1: counts
  * n_r,j (round/ceil formulas) and shifts E_S,j = E_S,j-1 + ((E_max-E_min)/N)
  * (n_r,j + n_r,j-1)/2 with E_S,0 = E_min, n_r,0 = 0.  e_min/e_max are the

@@ -70,9 +70,13 @@ def residual_norms(apply_A, eps: np.ndarray, U: np.ndarray) -> np.ndarray:
     return np.linalg.norm(R, axis=0) / np.linalg.norm(U, axis=0)
 
 
-def arpack_window(wire, sigma: float, n_req: int, tol: float = 1e-12, seed: int = 0,
+def arpack_window(wire, sigma: complex, n_req: int, tol: float = 1e-12, seed: int = 0,
                   ncv: int | None = None, maxiter: int | None = None, bc: int = stencil.BC_ODD):
     """The paper's per-window solve: ARPACK 'SM' on x -> (A - sigma) x (Eq. (3)).
+
+    sigma is real for the paper's windows; a complex sigma gives a window of
+    the two-dimensional partition Section 2 names for strongly non-Hermitian
+    problems.
 
     Returns eps (Re-sorted, shifted back by sigma) and eigenvectors scaled to
     unit 2-norm.  ARPACK's implicitly restarted Arnoldi applies the shifted

@@ -119,6 +119,20 @@ def merge_samples(spectrum, sample, prev_top: float, tol: float):
     return out
 
 
+def complex_shift_window(eps, sigma: complex, n_req: int):
+    """Indices of the eigenvalues a window with a complex shift delivers.
+
+    Section 2 (after Eq. 5) extends the partition to strongly non-Hermitian
+    problems with complex shifts on a two-dimensional grid; each window keeps
+    the SM rule of Eq. 3 on A - sigma: the n_req eigenvalues nearest sigma in
+    the complex plane, ties broken by (Re, Im) as for real shifts.
+    """
+    e = np.asarray(eps, dtype=np.complex128)
+    d = np.abs(e - complex(sigma))
+    order = np.lexsort((e.imag, e.real, d))
+    return order[:n_req]
+
+
 def combine(eps_list, U_list, eq_rtol: float = 1e-8, drop_tol: float = 1e-6):
     """Algorithm 2 over windows given in shift order.
 

@@ -26,7 +26,8 @@ ARITH_DS, ARITH_F64 = 2, 1
 CONTRACT_F64, CONTRACT_F32 = 0, 1
 
 # Every entry point declared in include/swi.h.
-EXPORTS = ("swi_create", "swi_set_potential", "swi_set_absorber", "swi_set_windows", "swi_plan_windows", "swi_plan_windows_sampled",
+EXPORTS = ("swi_create", "swi_set_potential", "swi_set_absorber", "swi_set_windows", "swi_set_windows_complex",
+           "swi_plan_windows", "swi_plan_windows_sampled",
            "swi_apply", "swi_apply_ds", "swi_apply_c64", "swi_solve", "swi_solve_more", "swi_fill_holes",
            "swi_get_windows", "swi_refine", "swi_get_window_info", "swi_get_eigenpairs", "swi_copy_eigenpairs",
            "swi_set_eigenpairs", "swi_residuals", "swi_transmission", "swi_set_contraction", "swi_grad", "swi_profile",
@@ -108,6 +109,7 @@ def load(path: str = LIB_PATH):
         "swi_set_potential": (I, [VP, VP, I]),
         "swi_set_absorber": (I, [VP, VP, VP, I]),
         "swi_set_windows": (I, [VP, I, VP, VP]),
+        "swi_set_windows_complex": (I, [VP, I, VP, VP, VP]),
         "swi_plan_windows": (I, [VP, I, I, D, D, D, VP, VP]),
         "swi_plan_windows_sampled": (I, [VP, I, I, P(PlanOpts), VP, VP, P(PlanInfo)]),
         "swi_apply": (I, [VP, I, VP, VP, VP, I]),
@@ -225,6 +227,12 @@ class Context:
     def set_windows(self, sigma, n_req):
         s, n = _c_arr(sigma, np.float64), _c_arr(n_req, np.int32)
         return self._check(self._lib.swi_set_windows(self._h, len(s), _ptr(s), _ptr(n)))
+
+    def set_windows_complex(self, sigma, n_req):
+        """Windows at complex shifts (sigma: complex array, increasing by (Re, Im))."""
+        z = np.asarray(sigma, dtype=np.complex128)
+        re, im, n = _c_arr(z.real, np.float64), _c_arr(z.imag, np.float64), _c_arr(n_req, np.int32)
+        return self._check(self._lib.swi_set_windows_complex(self._h, len(re), _ptr(re), _ptr(im), _ptr(n)))
 
     def plan_windows(self, n_r, p, e_min, e_max, inflate=1.0):
         s = np.zeros(p)

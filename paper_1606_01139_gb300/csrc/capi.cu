@@ -307,6 +307,8 @@ using namespace swi::host;
 void swi::host::record_windows(swi_ctx* c, const std::vector<double2>& eps_all, const std::vector<int>& win_of,
                                int nwin) {
   c->last_sigma = c->sigma;
+  c->last_complex = false;
+  for (double v : c->sigma_im) c->last_complex = c->last_complex || v != 0.0;
   c->last_eps_win = eps_all;
   c->last_win_of = win_of;
   c->last_holes.assign(std::max(0, nwin - 1), 0);
@@ -319,6 +321,8 @@ namespace {
 swi_status do_solve(swi_ctx* c, const swi_solve_opts* o, swi_solve_info* info) {
   if (!c->has_V || !c->has_G) return fail(c, SWI_ESTATE, "potential and absorbers must be set before solve");
   if (c->sigma.empty()) return fail(c, SWI_ESTATE, "windows must be set before solve");
+  for (double v : c->sigma_im)
+    if (v != 0.0) return fail(c, SWI_EINVAL, "complex shifts need windows of 1 or 2 vectors (double-single or mixed)");
   swi_solve_opts opt;
   std::memset(&opt, 0, sizeof(opt));
   if (o) opt = *o;
@@ -1169,6 +1173,25 @@ swi_status swi_set_windows(swi_ctx* c, int p, const double* sigma, const int* n_
       if (j > 0 && !(sigma[j] > sigma[j - 1])) return fail(c, SWI_EINVAL, "shifts must be strictly increasing");
     }
     c->sigma.assign(sigma, sigma + p);
+    c->sigma_im.clear();  // real shifts
+    c->nreq.assign(n_req, n_req + p);
+    return SWI_OK;
+  });
+}
+
+swi_status swi_set_windows_complex(swi_ctx* c, int p, const double* sigma_re, const double* sigma_im,
+                                   const int* n_req) {
+  return guarded(c, [&]() -> swi_status {
+    if (p < 1 || !sigma_re || !sigma_im || !n_req) return fail(c, SWI_EINVAL, "need p >= 1 windows");
+    if (p > swi::kMaxBatch) return fail(c, SWI_EINVAL, "at most 64 windows");
+    for (int j = 0; j < p; ++j) {
+      if (!std::isfinite(sigma_re[j]) || !std::isfinite(sigma_im[j])) return fail(c, SWI_EINVAL, "non-finite shift");
+      if (n_req[j] < 1) return fail(c, SWI_EINVAL, "each window needs n_req >= 1");
+      if (j > 0 && !(sigma_re[j] > sigma_re[j - 1] || (sigma_re[j] == sigma_re[j - 1] && sigma_im[j] > sigma_im[j - 1])))
+        return fail(c, SWI_EINVAL, "shifts must be strictly increasing by (Re, Im)");
+    }
+    c->sigma.assign(sigma_re, sigma_re + p);
+    c->sigma_im.assign(sigma_im, sigma_im + p);
     c->nreq.assign(n_req, n_req + p);
     return SWI_OK;
   });
@@ -1207,6 +1230,7 @@ swi_status swi_plan_windows(swi_ctx* c, int n_r, int p, double e_min, double e_m
     if (sigma_out) std::copy(sg.begin(), sg.end(), sigma_out);
     if (n_req_out) std::copy(rq.begin(), rq.end(), n_req_out);
     c->sigma = sg;
+    c->sigma_im.clear();  // real shifts
     c->nreq = rq;
     return SWI_OK;
   });
@@ -1382,6 +1406,7 @@ swi_status swi_set_eigenpairs(swi_ctx* c, int n, const void* eps, const void* U,
     c->have_RL = false;
     c->resid.clear();
     c->last_sigma.clear();  // restored pairs carry no window records
+    c->last_complex = false;
     c->last_eps_win.clear();
     c->last_win_of.clear();
     c->last_holes.clear();

@@ -312,17 +312,17 @@ __global__ void __launch_bounds__(kDenseThreads) schur_kernel(const __grid_const
   }
   __syncthreads();
 
-  // ---------------- select the 'keep' Ritz values closest to the shift (smallest |theta|)
+  // ---------------- select the 'keep' Ritz values closest to the shift (smallest |theta - i sig_im|)
   // rank by (|theta|, Re, Im, index)
   __shared__ int s_sel[1024];
   for (int i = tid; i < m; i += blockDim.x) {
     const double2 ti = HH(i, i);
-    const double ai = cabs(ti);
+    const double ai = cabs(make_double2(ti.x, ti.y - J.sig_im));
     int rank = 0;
     for (int q = 0; q < m; ++q) {
       if (q == i) continue;
       const double2 tq = HH(q, q);
-      const double aq = cabs(tq);
+      const double aq = cabs(make_double2(tq.x, tq.y - J.sig_im));
       bool less = aq < ai || (aq == ai && (tq.x < ti.x || (tq.x == ti.x && (tq.y < ti.y || (tq.y == ti.y && q < i)))));
       rank += less ? 1 : 0;
     }
@@ -336,8 +336,8 @@ __global__ void __launch_bounds__(kDenseThreads) schur_kernel(const __grid_const
     while (k < m - 1 && k < J.kmax) {
       double a_in = -1.0, a_out = -1.0;
       for (int q = 0; q < m; ++q) {
-        if (s_sel[q] == k - 1) a_in = cabs(HH(q, q));
-        if (s_sel[q] == k) a_out = cabs(HH(q, q));
+        if (s_sel[q] == k - 1) a_in = cabs(make_double2(HH(q, q).x, HH(q, q).y - J.sig_im));
+        if (s_sel[q] == k) a_out = cabs(make_double2(HH(q, q).x, HH(q, q).y - J.sig_im));
       }
       if (a_out - a_in <= 1e-10 * fmax(1.0, a_in)) ++k;
       else break;
@@ -427,10 +427,10 @@ __global__ void __launch_bounds__(kDenseThreads) schur_kernel(const __grid_const
     // wanted = the nwant smallest |theta| among the kept
     int nconv = 0;
     for (int i = 0; i < kk; ++i) {
-      const double ai = cabs(HH(i, i));
+      const double ai = cabs(make_double2(HH(i, i).x, HH(i, i).y - J.sig_im));
       int rank = 0;
       for (int q = 0; q < kk; ++q) {
-        const double aq = cabs(HH(q, q));
+        const double aq = cabs(make_double2(HH(q, q).x, HH(q, q).y - J.sig_im));
         if (aq < ai || (aq == ai && q < i)) ++rank;
       }
       if (rank < J.nwant && J.resid[i] <= J.tol_abs) ++nconv;
@@ -452,10 +452,10 @@ __global__ void ritz_kernel(const __grid_constant__ RitzBatch batch) {
   // wanted = nwant smallest |theta| among the leading kk, then ordered by (Re, Im)
   for (int i = tid; i < kk; i += blockDim.x) {
     const double2 ti = J.theta[i];
-    const double ai = cabs(ti);
+    const double ai = cabs(make_double2(ti.x, ti.y - J.sig_im));
     int rank = 0;
     for (int q = 0; q < kk; ++q) {
-      const double aq = cabs(J.theta[q]);
+      const double aq = cabs(make_double2(J.theta[q].x, J.theta[q].y - J.sig_im));
       if (aq < ai || (aq == ai && q < i)) ++rank;
     }
     widx[i] = rank < J.nwant ? 1 : 0;

@@ -81,6 +81,7 @@ struct swi_ctx {
   bool has_V = false, has_G = false;
   double maxabsV = 0.0, maxG = 0.0;
   std::vector<double> sigma;
+  std::vector<double> sigma_im;  // imaginary parts of complex shifts (empty: all real)
   std::vector<int> nreq;
   // windows of the current pairs: shifts (shift order), the eigenvalues each
   // window delivered before the merge, and the merge's interface flags
@@ -89,6 +90,7 @@ struct swi_ctx {
   std::vector<double2> last_eps_win;
   std::vector<int> last_win_of;
   std::vector<int> last_holes;
+  bool last_complex = false;  // the current pairs came from windows with complex shifts
   // current pairs
   int npairs = 0;
   DevMem eps, U;  // [n], [N][n]

@@ -502,15 +502,15 @@ __global__ void __launch_bounds__(kThreads) schur_ds_kernel(const __grid_constan
   }
   __syncthreads();
 
-  // ---------------- selection: rank by (|theta|, Re, Im, index) in FP64 of the diagonal
+  // ---------------- selection: rank by (|theta - i sig_im|, Re, Im, index) in FP64 of the diagonal
   for (int i = tid; i < m; i += blockDim.x) {
     const double2 ti = cto(HD(i, i));
-    const double ai = hypot(ti.x, ti.y);
+    const double ai = hypot(ti.x, ti.y - J.sig_im);
     int rank = 0;
     for (int q = 0; q < m; ++q) {
       if (q == i) continue;
       const double2 tq = cto(HD(q, q));
-      const double aq = hypot(tq.x, tq.y);
+      const double aq = hypot(tq.x, tq.y - J.sig_im);
       const bool less = aq < ai || (aq == ai && (tq.x < ti.x || (tq.x == ti.x && (tq.y < ti.y || (tq.y == ti.y && q < i)))));
       rank += less ? 1 : 0;
     }
@@ -523,8 +523,8 @@ __global__ void __launch_bounds__(kThreads) schur_ds_kernel(const __grid_constan
       double a_in = -1.0, a_out = -1.0;
       for (int q = 0; q < m; ++q) {
         const double2 tq = cto(HD(q, q));
-        if (s_sel[q] == k - 1) a_in = hypot(tq.x, tq.y);
-        if (s_sel[q] == k) a_out = hypot(tq.x, tq.y);
+        if (s_sel[q] == k - 1) a_in = hypot(tq.x, tq.y - J.sig_im);
+        if (s_sel[q] == k) a_out = hypot(tq.x, tq.y - J.sig_im);
       }
       if (a_out - a_in <= 1e-10 * fmax(1.0, a_in)) ++k;
       else break;
@@ -719,10 +719,12 @@ __global__ void __launch_bounds__(kThreads) schur_ds_kernel(const __grid_constan
   if (tid == 0) {
     int nconv = 0;
     for (int i = 0; i < kk; ++i) {
-      const double ai = swi::cabs(H[(long long)i * ld + i]);
+      const double2 ti = H[(long long)i * ld + i];
+      const double ai = swi::cabs(make_double2(ti.x, ti.y - J.sig_im));
       int rank = 0;
       for (int q = 0; q < kk; ++q) {
-        const double aq = swi::cabs(H[(long long)q * ld + q]);
+        const double2 tq = H[(long long)q * ld + q];
+        const double aq = swi::cabs(make_double2(tq.x, tq.y - J.sig_im));
         if (aq < ai || (aq == ai && q < i)) ++rank;
       }
       if (rank < J.nwant && J.resid[i] <= J.tol_abs) ++nconv;

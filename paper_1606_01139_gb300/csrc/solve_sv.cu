@@ -50,6 +50,7 @@ template <bool DS>
 struct SvWin {
   using T = typename SV<DS>::T;
   double sigma = 0.0;  // the shift the stencil applies (rounded to FP32 in the complex64 form)
+  double sig_im = 0.0; // imaginary part of a complex shift (applied by the selection only)
   int nreq = 0, m = 0, keep = 0, ldq = 0, ldh = 0, col = 0;
   int p = 0;  // the newest block is basis columns [p, p + nb) (the ones expanded next)
   DevMem Q, H, Z, S, Bz, theta, resid, Yw, eps_w, res_w, Hw, Zw, C1, C2, Z32, rinv, part;  // part: FP64 chunk partials
@@ -141,6 +142,7 @@ swi_status solve_sv(swi_ctx* c, const swi_solve_opts& opt, swi_solve_info* info)
     win[j].reset(new Win());
     Win& w = *win[j];
     w.sigma = DS ? c->sigma[j] : (double)(float)c->sigma[j];
+    w.sig_im = c->sigma_im.size() == c->sigma.size() ? c->sigma_im[j] : 0.0;
     w.nreq = c->nreq[j];
     w.col = j;
     int keep = opt.keep > 0 ? opt.keep : std::max(w.nreq + (w.nreq + 1) / 2, w.nreq + nb);
@@ -357,7 +359,7 @@ swi_status solve_sv(swi_ctx* c, const swi_solve_opts& opt, swi_solve_info* info)
     sb.job[0] = swi::SchurJob{H, w.Z.template as<double2>(), H + (long long)w.p * w.ldh, w.Bz.template as<double2>(),
                               w.theta.template as<double2>(), w.resid.template as<double>(), w.S.template as<double2>(),
                               c->ordinfo.as<int>() + 4 * j, w.p, w.ldh, nb, keep_eff, w.nreq, w.m - nb, tol_abs,
-                              w.Hw.p, w.Zw.p};
+                              w.Hw.p, w.Zw.p, w.sig_im};
     {
       ProfScope ps(c, SWI_K_SCHUR, 0.0, 0.0, sj);
       if (f64) swi::launch_schur_batch(sb, sj, &c->launches);
@@ -395,7 +397,7 @@ swi_status solve_sv(swi_ctx* c, const swi_solve_opts& opt, swi_solve_info* info)
       fin.job[0] = swi::RitzJob{w.Z.template as<double2>(), w.S.template as<double2>(), w.theta.template as<double2>(),
                                 w.resid.template as<double>(), c->ordinfo.as<int>() + 4 * j, w.Yw.template as<double2>(),
                                 w.eps_w.template as<double2>(), w.res_w.template as<double>(), n, w.ldh, w.nreq,
-                                w.nreq, w.sigma};
+                                w.nreq, w.sigma, w.sig_im};
       swi::RowGemmBatch rb;
       rb.n = 1;
       rb.job[0] = swi::RowGemmJob{Qb, w.Yw.template as<double2>(), nullptr, c->Uall.as<double2>() + out_off[j], ldb,

@@ -200,6 +200,8 @@ struct SchurJob {
   double tol_abs;    // absolute residual threshold
   void* Hw;          // [ld][ld] 16-byte work entries (double-single kernel only)
   void* Zw;          // [ld][ld] 16-byte work entries (double-single kernel only)
+  double sig_im;     // imaginary part of a complex shift: the selection ranks |theta - i sig_im|
+                     // (theta: eigenvalues of the projection of A - Re sigma)
 };
 struct SchurBatch {
   int n;
@@ -223,6 +225,7 @@ struct RitzJob {
   double* res_out;   // [nwant]
   int m, ld, ldy, nwant;
   double sigma;
+  double sig_im;     // as SchurJob::sig_im (eps = theta + sigma, sigma the real shift applied)
 };
 struct RitzBatch {
   int n;

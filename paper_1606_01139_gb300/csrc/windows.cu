@@ -48,6 +48,7 @@ swi_status do_solve_more(swi_ctx* c, int p, const double* sigma, const int* n_re
   if (o) opt = *o;
   if (c->npairs <= 0) {  // nothing stored: a plain solve
     c->sigma.assign(sigma, sigma + p);
+    c->sigma_im.clear();  // real shifts
     c->nreq.assign(n_req, n_req + p);
     return solve(c, &opt, info);
   }
@@ -86,6 +87,7 @@ swi_status do_solve_more(swi_ctx* c, int p, const double* sigma, const int* n_re
   }
   // the new windows on their own (all their merged pairs kept)
   c->sigma.assign(sigma, sigma + p);
+  c->sigma_im.clear();  // real shifts
   c->nreq.assign(n_req, n_req + p);
   swi_solve_opts inner = opt;
   inner.n_keep = 0;
@@ -143,6 +145,7 @@ swi_status do_solve_more(swi_ctx* c, int p, const double* sigma, const int* n_re
   merge_pairs(c, c->Uall.as<double2>(), n_all, eps_all, win_of, p_all, eq_rtol, drop_tol, opt.n_keep, minfo);
   // the windows of the union and the eigenvalues each delivered
   c->sigma.resize(p_all);
+  c->sigma_im.clear();  // real shifts
   for (int r = 0; r < p_all; ++r) c->sigma[r] = sig_all[ord[r]];
   std::vector<double2> epsw;
   std::vector<int> winw;
@@ -198,6 +201,7 @@ swi_status do_fill_holes(swi_ctx* c, double e_min, double e_max, int max_rounds,
   if (!(e_max > e_min) || !std::isfinite(e_min) || !std::isfinite(e_max))
     return fail(c, SWI_EINVAL, "need finite e_max > e_min");
   if (c->npairs <= 0 || c->last_sigma.empty()) return fail(c, SWI_ESTATE, "no solve to fill holes in");
+  if (c->last_complex) return fail(c, SWI_EINVAL, "hole filling places windows on the real axis: the last solve used complex shifts");
   const int rounds = max_rounds > 0 ? max_rounds : 4;
   const double spacing = (e_max - e_min) / c->N;  // uniform-density spacing of Algorithm 1
   int added = 0;
@@ -330,6 +334,7 @@ swi_status do_plan_sampled(swi_ctx* c, int n_r, int p, const swi_plan_opts* po, 
     const double sg[2] = {vmin - 1.0, an + 1.0};
     const int rq[2] = {2, 2};
     c->sigma.assign(sg, sg + 2);
+    c->sigma_im.clear();  // real shifts
     c->nreq.assign(rq, rq + 2);
     swi_solve_info inf;
     const swi_status st = solve(c, &so, &inf);
@@ -346,6 +351,7 @@ swi_status do_plan_sampled(swi_ctx* c, int n_r, int p, const swi_plan_opts* po, 
   int samples = 0;
   while ((int)spec.size() < n_r && samples < max_samples) {
     c->sigma.assign(1, sig);
+    c->sigma_im.clear();  // real shifts
     c->nreq.assign(1, q);
     swi_solve_info inf;
     const swi_status st = solve(c, &so, &inf);
@@ -396,6 +402,7 @@ swi_status do_plan_sampled(swi_ctx* c, int n_r, int p, const swi_plan_opts* po, 
   for (size_t j = 1; j < sg.size(); ++j)
     if (!(sg[j] > sg[j - 1])) return fail(c, SWI_EINVAL, "planner: coincident shifts (a degenerate run)");
   c->sigma = sg;
+  c->sigma_im.clear();  // real shifts
   c->nreq = rq;
   if (sigma_out) std::copy(sg.begin(), sg.end(), sigma_out);
   if (n_req_out) std::copy(rq.begin(), rq.end(), n_req_out);

@@ -101,3 +101,22 @@ def test_arpack_windows_union_equals_dense_lowest():
         P_dense = eigen.cluster_projector(U, g)
         P_win = eigen.cluster_projector(U_sel, g)
         np.testing.assert_allclose(P_win, P_dense, atol=1e-8)
+
+
+def test_arpack_complex_shift_windows_are_the_nearest_eigenvalues():
+    # Section 2's complex shifts: ARPACK 'SM' on A - sigma for sigma off the
+    # real axis returns the eigenvalues nearest sigma in the complex plane,
+    # which on a 20-bohr wire (the absorbers cover only its ends, so -Im eps
+    # spreads over [0, 0.33]) differ between a shift near the axis and one
+    # below it at the same real part
+    w = W.make_wire(6, 6, 40, 0.5, 6, 3)
+    eps, U = eigen.dense_spectrum(_dense(w))
+    sets = []
+    for s in (1.2 - 0.3j, 1.2 - 0.01j):
+        idx = partition.complex_shift_window(eps, s, 6)
+        d = np.sort(np.abs(eps - s))
+        assert d[6] - d[5] > 0.1 * d[5]  # a clear cut
+        e, V = eigen.arpack_window(w, s, 6, tol=1e-13, seed=1)
+        np.testing.assert_allclose(np.sort_complex(e), np.sort_complex(eps[idx]), atol=1e-10)
+        sets.append(set(int(i) for i in idx))
+    assert sets[0] != sets[1]

@@ -127,3 +127,15 @@ def test_combine_gap_leaves_hole_flag():
     e, U, win, holes = partition.combine([np.array([0.1, 0.2]), np.array([0.5, 0.6])],
                                          [np.stack(vs[:2], 1), np.stack(vs[2:], 1)])
     assert len(e) == 4 and holes == [True]
+
+
+def test_complex_shift_window_by_hand():
+    # distances to sigma = 0.5 - 0.5i: 0 -> 0.707, 1 -> 0.707, -i -> 0.707,
+    # 2 - 0.5i -> 1.5, -1 -> 1.58; the three-way tie is broken by (Re, Im):
+    # -i (Re 0, Im -1), then 0 (Re 0, Im 0), then 1
+    eps = np.array([0.0, 1.0, -1j, 2.0 - 0.5j, -1.0])
+    assert list(partition.complex_shift_window(eps, 0.5 - 0.5j, 2)) == [2, 0]
+    assert list(partition.complex_shift_window(eps, 0.5 - 0.5j, 3)) == [2, 0, 1]
+    assert list(partition.complex_shift_window(eps, 2.0 - 0.6j, 1)) == [3]
+    # a real shift: the eigenvalues nearest it on the real axis
+    assert sorted(partition.complex_shift_window(eps, -0.9, 2)) == [0, 4]

@@ -280,6 +280,28 @@ swi_status swi_apply_c64(swi_ctx* ctx, int nvec, const float* sigma, const void*
  * available (partial result); SWI_ESTATE if windows/potential are unset. */
 swi_status swi_solve(swi_ctx* ctx, const swi_solve_opts* opts, swi_solve_info* info);
 
+/* The batching form: several independent systems (contexts of uneven grids,
+ * potentials, absorbers and windows, all on one device) solved at once.  The
+ * partition's independence (Section 2.1: windows, and here whole systems,
+ * need nothing from one another until the merge) lets every system run its
+ * swi_solve on a host worker and a stream of its own, so the device
+ * interleaves the systems' stencil, Gram-Schmidt and Schur launches.  Each
+ * context ends with its own merged pairs, as after swi_solve.
+ *   n       number of contexts (>= 1, distinct, same device);
+ *   ctxs    the contexts, each used by one worker at a time (no other call on
+ *           them may run meanwhile);
+ *   opts    as swi_solve, for every context (may be NULL);
+ *   workers host workers (<= 0: min(n, hardware threads));
+ *   infos   n records, status n codes (either may be NULL).
+ * Returns SWI_OK when every solve did, else the first other status by context
+ * order (each context's message in swi_last_error(ctx)).  The complex64
+ * stencil's bounded-wait flag is per device, so with concurrent
+ * SWI_PREC_MIXED solves a wait that ran out is reported by whichever solve
+ * reads the flag first.  Errors: SWI_EINVAL (n < 1, NULL or repeated
+ * contexts, contexts on different devices; message in swi_last_error(NULL)). */
+swi_status swi_solve_batch(int n, swi_ctx* const* ctxs, const swi_solve_opts* opts, int workers,
+                           swi_solve_info* infos, swi_status* status);
+
 /* Continuation run (Section 2: a computed set of pairs is extended by adding
  * windows while the old pairs are kept; the paper's Conclusions): solve the p
  * new windows (sigma strictly increasing, n_req >= 1, host arrays) with the

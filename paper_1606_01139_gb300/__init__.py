@@ -28,7 +28,7 @@ CONTRACT_F64, CONTRACT_F32 = 0, 1
 # Every entry point declared in include/swi.h.
 EXPORTS = ("swi_create", "swi_set_potential", "swi_set_absorber", "swi_set_windows", "swi_set_windows_complex",
            "swi_plan_windows", "swi_plan_windows_sampled",
-           "swi_apply", "swi_apply_ds", "swi_apply_c64", "swi_solve", "swi_solve_more", "swi_fill_holes",
+           "swi_apply", "swi_apply_ds", "swi_apply_c64", "swi_solve", "swi_solve_batch", "swi_solve_more", "swi_fill_holes",
            "swi_get_windows", "swi_refine", "swi_get_window_info", "swi_get_eigenpairs", "swi_copy_eigenpairs",
            "swi_set_eigenpairs", "swi_residuals", "swi_transmission", "swi_set_contraction", "swi_grad", "swi_profile",
            "swi_profile_read", "swi_transmission_noalloc", "swi_check_schur", "swi_last_error", "swi_launch_count",
@@ -116,6 +116,7 @@ def load(path: str = LIB_PATH):
         "swi_apply_ds": (I, [VP, I, VP, VP, VP, I]),
         "swi_apply_c64": (I, [VP, I, VP, VP, VP, I]),
         "swi_solve": (I, [VP, P(SolveOpts), P(SolveInfo)]),
+        "swi_solve_batch": (I, [I, VP, P(SolveOpts), I, P(SolveInfo), VP]),
         "swi_solve_more": (I, [VP, I, VP, VP, P(SolveOpts), P(SolveInfo)]),
         "swi_fill_holes": (I, [VP, D, D, I, P(SolveOpts), P(SolveInfo), P(I)]),
         "swi_get_windows": (I, [VP, I, VP, VP, P(I)]),
@@ -462,6 +463,29 @@ class Context:
         self._check(self._lib.swi_profile_read(self._h, arr))
         return {name: {"launches": arr[k].launches, "ms": arr[k].ms, "flops": arr[k].flops,
                        "bytes": arr[k].bytes} for k, name in enumerate(KERNEL_CLASSES)}
+
+
+def solve_batch(contexts, block=2, rel_tol=1e-10, max_basis=0, keep=0, max_matvecs=0, eq_rtol=0.0, drop_tol=0.0,
+                seed=1, n_keep=0, arith=ARITH_DS, workers=0):
+    """swi_solve_batch: the windows of several contexts (systems of uneven grids) solved at once.
+
+    Returns one info dict per context (with "status"); contexts keep their merged pairs."""
+    lib = load()
+    n = len(contexts)
+    handles = (C.c_void_p * n)(*[c._h for c in contexts])
+    o = SolveOpts(block=block, max_basis=max_basis, keep=keep, max_matvecs=max_matvecs, rel_tol=rel_tol,
+                  eq_rtol=eq_rtol, drop_tol=drop_tol, seed=seed, n_keep=n_keep, arith=arith)
+    infos = (SolveInfo * n)()
+    st = np.zeros(n, dtype=np.int32)
+    rc = lib.swi_solve_batch(n, C.cast(handles, C.c_void_p), C.byref(o), int(workers), infos, _ptr(st))
+    if rc == SWI_EINVAL and np.all(st == 0):
+        raise SwiError(rc, lib.swi_last_error(None).decode())
+    out = []
+    for k in range(n):
+        d = infos[k].as_dict()
+        d["status"] = STATUS_NAMES[int(st[k])]
+        out.append(d)
+    return out
 
 
 def transmission_function():

@@ -11,6 +11,7 @@
 // term the relative error is ~2^-48; a dot product of K terms is accurate to
 // ~K 2^-48, i.e. ~1e-13 for the bases used here, and every reduction across
 // CTAs is done in FP64 in a fixed order.
+#include <atomic>
 #include <algorithm>
 
 #include "ds.cuh"
@@ -577,12 +578,12 @@ __global__ void __launch_bounds__(256) rowgemm_df_kernel(const __grid_constant__
 // once for each device this process launches on (bit d of `done`; devices
 // past 63 set it on every call).
 template <class K>
-void set_smem_attr_once(K kernel, int bytes, unsigned long long& done) {
+void set_smem_attr_once(K kernel, int bytes, std::atomic<unsigned long long>& done) {
   int dev = 0;
   SWI_CUDA_TRY(cudaGetDevice(&dev));
-  if (dev < 64 && ((done >> dev) & 1ull)) return;
+  if (dev < 64 && ((done.load() >> dev) & 1ull)) return;
   SWI_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  if (dev < 64) done |= 1ull << dev;
+  if (dev < 64) done.fetch_or(1ull << dev);
 }
 
 void launch_gram_df(const GramBatch& b, int N, const double* w, int bilinear, double2* work, size_t work_elems,
@@ -599,7 +600,7 @@ void launch_gram_df(const GramBatch& b, int N, const double* w, int bilinear, do
   // Gram-Schmidt projections): tensor cores with the exact digit split
   bool tensor = !w && !bilinear && maxny <= 16 && maxnx > 16;
   if (tensor) {
-    static unsigned long long attr = 0;  // devices whose attribute is set
+    static std::atomic<unsigned long long> attr{0};  // devices whose attribute is set (solves may run on several host threads)
     set_smem_attr_once(gram_oz_kernel, (int)oz::kSmem, attr);
     const int tiles_i = (maxnx + oz::kTI - 1) / oz::kTI;
     int nch = (32 * 152 + tiles_i * b.n - 1) / (tiles_i * b.n);
@@ -671,7 +672,7 @@ void launch_rowgemm_df(const RowGemmBatch& b, int N, cudaStream_t s, long long* 
   } else {
     // long contractions (the Gram-Schmidt update W -= Q C, the restart rotation
     // Q Z): tensor cores with the exact digit split
-    static unsigned long long attr = 0;  // devices whose attribute is set
+    static std::atomic<unsigned long long> attr{0};  // devices whose attribute is set (solves may run on several host threads)
     set_smem_attr_once(rowgemm_oz_kernel, (int)oz::kSmem, attr);
     dim3 grid((N + oz::kTI - 1) / oz::kTI, (maxc + oz::kTJ - 1) / oz::kTJ, b.n);
     rowgemm_oz_kernel<<<grid, 256, oz::kSmem, s>>>(b, N);

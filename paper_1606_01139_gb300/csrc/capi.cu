@@ -15,6 +15,8 @@
 #include <new>
 #include <string>
 #include <mutex>
+#include <atomic>
+#include <thread>
 #include <vector>
 
 #include "merge.cuh"
@@ -1324,6 +1326,75 @@ static swi_status solve_dispatch(swi_ctx* c, const swi_solve_opts* opts, swi_sol
 
 swi_status swi_solve(swi_ctx* c, const swi_solve_opts* opts, swi_solve_info* info) {
   return guarded(c, [&]() -> swi_status { return solve_dispatch(c, opts, info); });
+}
+
+swi_status swi_solve_batch(int n, swi_ctx* const* ctxs, const swi_solve_opts* opts, int workers,
+                           swi_solve_info* infos, swi_status* status) {
+  if (n < 1 || !ctxs) return fail(nullptr, SWI_EINVAL, "swi_solve_batch: need n >= 1 contexts");
+  {
+    std::vector<const swi_ctx*> seen;
+    for (int i = 0; i < n; ++i) {
+      if (!ctxs[i]) return fail(nullptr, SWI_EINVAL, "swi_solve_batch: null context");
+      if (ctxs[i]->device != ctxs[0]->device)
+        return fail(nullptr, SWI_EINVAL, "swi_solve_batch: contexts on different devices");
+      seen.push_back(ctxs[i]);
+    }
+    std::sort(seen.begin(), seen.end());
+    if (std::adjacent_find(seen.begin(), seen.end()) != seen.end())
+      return fail(nullptr, SWI_EINVAL, "swi_solve_batch: a context appears twice");
+  }
+  // each system's solve on a host worker of its own (its own stream and side
+  // streams): the device interleaves the systems' launches
+  std::vector<swi_status> st(n, SWI_OK);
+  std::atomic<int> next{0};
+  int nw = workers > 0 ? workers : (int)std::thread::hardware_concurrency();
+  nw = std::max(1, std::min(nw, n));
+  auto work = [&]() {
+    for (;;) {
+      const int i = next.fetch_add(1);
+      if (i >= n) return;
+      swi_ctx* c = ctxs[i];
+      swi_solve_info* inf = infos ? infos + i : nullptr;
+      st[i] = guarded(c, [&]() -> swi_status {
+        // a stream of the solve's own (contexts made on one caller stream would
+        // otherwise serialise), ordered after and before the context's stream
+        struct Own {
+          cudaStream_t s = nullptr;
+          cudaEvent_t e = nullptr;
+          swi_ctx* c = nullptr;
+          cudaStream_t orig = nullptr;
+          ~Own() {
+            if (c) c->stream = orig;
+            if (e) cudaEventDestroy(e);
+            if (s) cudaStreamDestroy(s);
+          }
+        } own;
+        SWI_CUDA_TRY(cudaStreamCreateWithFlags(&own.s, cudaStreamNonBlocking));
+        SWI_CUDA_TRY(cudaEventCreateWithFlags(&own.e, cudaEventDisableTiming));
+        SWI_CUDA_TRY(cudaEventRecord(own.e, c->stream));
+        SWI_CUDA_TRY(cudaStreamWaitEvent(own.s, own.e, 0));
+        own.orig = c->stream;
+        own.c = c;
+        c->stream = own.s;
+        const swi_status r = solve_dispatch(c, opts, inf);
+        SWI_CUDA_TRY(cudaEventRecord(own.e, own.s));
+        SWI_CUDA_TRY(cudaStreamWaitEvent(own.orig, own.e, 0));
+        return r;
+      });
+    }
+  };
+  std::vector<std::thread> pool;
+  try {
+    for (int k = 1; k < nw; ++k) pool.emplace_back(work);
+  } catch (...) {
+    // fewer workers (thread creation failed): the ones running and this thread finish the batch
+  }
+  work();
+  for (auto& t : pool) t.join();
+  if (status) std::copy(st.begin(), st.end(), status);
+  for (int i = 0; i < n; ++i)
+    if (st[i] != SWI_OK) return st[i];
+  return SWI_OK;
 }
 
 swi_status swi_solve_more(swi_ctx* c, int p, const double* sigma, const int* n_req, const swi_solve_opts* opts,

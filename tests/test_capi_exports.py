@@ -71,6 +71,18 @@ def test_null_context_is_rejected_by_every_entry_taking_one(lib):
     assert L.swi_refine(None, None, None) == swi.SWI_EINVAL
     assert L.swi_residuals(None, None) == swi.SWI_EINVAL
     assert L.swi_transmission(None, 1, None, None) == swi.SWI_EINVAL
+    assert L.swi_set_contraction(None, 0) == swi.SWI_EINVAL
+    assert L.swi_set_windows_complex(None, 1, None, None, None) == swi.SWI_EINVAL
+
+
+def test_batch_solve_validates_its_arguments_before_any_device_call(lib):
+    import paper_1606_01139_gb300 as swi
+    swi.load()
+    L = swi._lib
+    assert L.swi_solve_batch(0, None, None, 0, None, None) == swi.SWI_EINVAL
+    nulls = (ctypes.c_void_p * 2)(None, None)
+    assert L.swi_solve_batch(2, ctypes.cast(nulls, ctypes.c_void_p), None, 0, None, None) == swi.SWI_EINVAL
+    assert b"null context" in L.swi_last_error(None)
 
 
 def test_binding_structs_match_the_header(tmp_path):

@@ -20,9 +20,13 @@ eigenpairs (explicit relative residual <= 1e-8) per second.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--no-cpu-baseline] [--no-extras] [--matvec-budget M] [--windows P]
+                    [--form step|batch|differentiation] [--batch-count K] [--batch-workers T]
 
 --matvec-budget and --windows shrink the run (fewer operator applications per
 window, only the lowest P windows) for profiling; the default is the workload.
+--form batch prints a line for the uneven batch of wires solved by one
+swi_solve_batch call; --form differentiation a line for T(E) and its adjoint on
+the 64x64x128 wire with 1000 pairs in FP32 and FP64-class contractions.
 
 N > 1 runs N independent replicas (one per rank, launched by torch.distributed.run);
 the value is the pairs of all ranks over the slowest rank's time.
@@ -418,6 +422,103 @@ def single_window(swi, stream, wire, lam, n_r, budget):
                     "budget, so the value is converged pairs/s at the bound; not part of the timed step"}
 
 
+def differentiation_form(swi, stream, sm_mhz, steps=3, warm=1):
+    """T(E) at 256 energies with the adjoint dL/dV over all N points and dL/dE, on the
+    64x64x128 wire with 1000 seeded synthetic pairs (timing does not depend on the pairs being
+    eigenpairs), once with the FP32 contractions and once with the FP64-class ones; the FP32
+    results are compared with the FP64-class run (parity-tested against the oracle at smaller
+    sizes).  Per-class device times from the library's CUDA-event profile."""
+    import torch
+    name = "wire_64x64x128"
+    cfg = W.CONFIGS[name]
+    wire = W.config_wire(name)
+    n, n_e = cfg["n_r"], cfg["n_E"]
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(cfg["seed"])
+    shape = (wire.N, n)
+    U = torch.complex(torch.randn(shape, generator=gen, device="cuda", dtype=torch.float64),
+                      torch.randn(shape, generator=gen, device="cuda", dtype=torch.float64)) / np.sqrt(2.0 * wire.N)
+    rng = np.random.default_rng(cfg["seed"])
+    eps_h = np.sort(rng.uniform(-1.0, 2.0, n)) - 1j * rng.uniform(0.01, 0.2, n)
+    eps = torch.tensor(eps_h, dtype=torch.complex128, device="cuda")
+    E = np.linspace(-1.1, 2.1, n_e)
+    w = rng.standard_normal(n_e)
+    ctx = swi.Context(wire.nx, wire.ny, wire.nz, wire.h, stream=stream.cuda_stream)
+    ctx.set_potential(wire.V)
+    ctx.set_absorber(wire.gamma_L, wire.gamma_R)
+    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    out, res = {}, {}
+    for mode, label in ((swi.CONTRACT_F64, "f64"), (swi.CONTRACT_F32, "f32")):
+        ctx.set_contraction(mode)
+        for _ in range(warm):
+            ctx.set_eigenpairs(eps, U)  # drops the cached projections: every step forms them
+            ctx.transmission(E)
+            ctx.grad(E, w)
+        ctx.profile(True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            ctx.set_eigenpairs(eps, U)
+            T = ctx.transmission(E)
+            dV, dE = ctx.grad(E, w)
+        torch.cuda.synchronize()
+        wall = (time.perf_counter() - t0) / steps
+        prof = ctx.profile_read()
+        ctx.profile(False)
+        res[label] = (T, dV, dE)
+        cls = {k: {"ms_per_step": round(prof[k]["ms"] / steps, 3),
+                   "TFLOP/s": round(prof[k]["flops"] / (prof[k]["ms"] / 1e3) / 1e12, 3) if prof[k]["ms"] > 0 else None}
+               for k in ("proj", "trans", "grad") if prof[k]["launches"]}
+        out[label] = {"s_per_step": round(wall, 4), "classes": cls}
+    (T64, dV64, dE64), (T32, dV32, dE32) = res["f64"], res["f32"]
+    out["f32_error_vs_f64"] = {
+        "T_max_abs": float(np.max(np.abs(T32 - T64))), "T_max": float(np.max(np.abs(T64))),
+        "dLdV_max_abs_rel": float(np.max(np.abs(dV32 - dV64)) / max(np.max(np.abs(dV64)), 1e-300)),
+        "dLdE_max_abs_rel": float(np.max(np.abs(dE32 - dE64)) / max(np.max(np.abs(dE64)), 1e-300))}
+    out["fp32_peak_TFLOP/s"] = round(fp32_peak, 1)
+    out["config"] = {"workload": name, "N": wire.N, "n_pairs": n, "n_E": n_e, "pairs": "seeded synthetic",
+                     "timing": "host clock with device synchronisation on both sides; classes by CUDA events"}
+    ctx.close()
+    return out
+
+
+def batch_form(swi, count, budget, workers):
+    """The uneven batch: `count` seeded wires (x, y axes 16..48, z twice 16..48, 8-40 wells,
+    32-256 pairs in 2-8 windows), each planned by the library's sampled planner (timed apart,
+    as the paper timed planning apart), then all solved by one swi_solve_batch call.  Counted:
+    pairs among each system's lowest n_r whose explicit FP64 residual is <= 1e-8."""
+    import torch
+    specs = W.batch_systems(seed=4, count=count)
+    ctxs, n_rs = [], []
+    t0 = time.perf_counter()
+    for sp in specs:
+        w = W.make_wire(sp["nx"], sp["ny"], sp["nz"], 0.5, sp["n_wells"], sp["seed"])
+        c = swi.Context(w.nx, w.ny, w.nz, w.h)
+        c.set_potential(w.V)
+        c.set_absorber(w.gamma_L, w.gamma_R)
+        sig, req, _ = c.plan_windows_sampled(sp["n_r"], sp["p"])
+        c.set_windows(sig, req)
+        ctxs.append(c)
+        n_rs.append(sp["n_r"])
+    t_plan = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    infos = swi.solve_batch(ctxs, block=BLOCK, rel_tol=REL_TOL, n_keep=0, max_matvecs=budget, workers=workers)
+    torch.cuda.synchronize()
+    t_solve = time.perf_counter() - t1
+    conv = 0
+    for c, n_r in zip(ctxs, n_rs):
+        r = c.residuals()[:n_r]
+        conv += int(np.sum(r <= REL_TOL))
+        c.close()
+    return {"metric": METRIC, "value": conv / t_solve, "unit": UNIT, "converged": conv,
+            "requested": int(sum(n_rs)), "solve_s": round(t_solve, 2), "plan_s": round(t_plan, 2),
+            "statuses": [i["status"] for i in infos],
+            "config": {"workload": f"uneven batch of {count} wires (seed 4)", "block": BLOCK,
+                       "matvec_budget_per_window": budget, "workers": workers,
+                       "timing": "host clock with device synchronisation on both sides"}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -428,6 +529,11 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the side measurements after the timed steps")
     ap.add_argument("--matvec-budget", type=int, default=MATVEC_BUDGET)
     ap.add_argument("--windows", type=int, default=0, help="use only the lowest P windows (0: all)")
+    ap.add_argument("--form", default="step", choices=["step", "batch", "differentiation"],
+                    help="step: the benchmark line; batch / differentiation: a line for the batching or "
+                         "differentiation form instead")
+    ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--batch-workers", type=int, default=0)
     args = ap.parse_args()
     rank = _env_int("RANK", 0)
     world = _env_int("WORLD_SIZE", 1)
@@ -451,6 +557,19 @@ def main():
     from paper_1606_01139_gb300 import build as B
     B.build()
     swi.load()
+    if args.form != "step":
+        stream = torch.cuda.current_stream()
+        if args.form == "batch":
+            line = batch_form(swi, args.batch_count, args.matvec_budget, args.batch_workers)
+        else:
+            sampler = ClockSampler(local)
+            sampler.start()
+            line = differentiation_form(swi, stream, 2070.0)
+            line["clocks"] = sampler.stop()
+        line["form"] = args.form
+        if rank == 0:
+            print(json.dumps(line))
+        return 0
 
     cfg = W.CONFIGS[WORKLOAD]
     wire = W.config_wire(WORKLOAD)

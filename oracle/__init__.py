@@ -14,8 +14,12 @@ parallel eigensolution efficiency in real-space electronic transport"):
 * ``eigen``     -- dense spectra (LAPACK zgeev through numpy), the U^T U = I
                    normalisation, and the paper's own per-window solver: ARPACK
                    'SM' on the shifted, never-inverted operator of Eq. (3).
-* ``partition`` -- Algorithm 1 (window counts, shifts, hole-filling window) and
-                   Algorithm 2 (combine, de-duplicate, hole flags).
+* ``partition`` -- Algorithm 1 (window counts, shifts, hole-filling window),
+                   Algorithm 2 (combine, de-duplicate, hole flags), the planner's
+                   sample merge, and the window a complex shift delivers (the
+                   two-dimensional partition of Section 2).
+* ``refine``    -- the FP64 residual-correction sweep (Rayleigh-Ritz on
+                   span[U, R] with the unconjugated pencil).
 * ``transport`` -- T(E) = Tr{G Gamma_R G^dagger Gamma_L} (Section 1) from the
                    spectral G and from a dense inverse; the adjoint gradient
                    dT/dV(r), dT/dE, and central finite differences.

@@ -291,7 +291,8 @@ swi_status swi_solve(swi_ctx* ctx, const swi_solve_opts* opts, swi_solve_info* i
  *   ctxs    the contexts, each used by one worker at a time (no other call on
  *           them may run meanwhile);
  *   opts    as swi_solve, for every context (may be NULL);
- *   workers host workers (<= 0: min(n, hardware threads));
+ *   workers host workers (<= 0: min(n, hardware threads)); they take the
+ *           systems largest first (grid points x requested pairs);
  *   infos   n records, status n codes (either may be NULL).
  * Returns SWI_OK when every solve did, else the first other status by context
  * order (each context's message in swi_last_error(ctx)).  The complex64

@@ -1346,13 +1346,24 @@ swi_status swi_solve_batch(int n, swi_ctx* const* ctxs, const swi_solve_opts* op
   // each system's solve on a host worker of its own (its own stream and side
   // streams): the device interleaves the systems' launches
   std::vector<swi_status> st(n, SWI_OK);
+  // largest systems first (grid points x requested pairs), so that a worker
+  // pool over uneven systems does not end on one large solve
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  auto work_of = [&](int i) {
+    long long r = 0;
+    for (int q : ctxs[i]->nreq) r += q;
+    return (double)ctxs[i]->N * (double)std::max(r, 1LL);
+  };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work_of(a) > work_of(b); });
   std::atomic<int> next{0};
   int nw = workers > 0 ? workers : (int)std::thread::hardware_concurrency();
   nw = std::max(1, std::min(nw, n));
   auto work = [&]() {
     for (;;) {
-      const int i = next.fetch_add(1);
-      if (i >= n) return;
+      const int t = next.fetch_add(1);
+      if (t >= n) return;
+      const int i = order[t];
       swi_ctx* c = ctxs[i];
       swi_solve_info* inf = infos ? infos + i : nullptr;
       st[i] = guarded(c, [&]() -> swi_status {
